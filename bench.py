@@ -1,0 +1,335 @@
+"""Benchmark of the fused phi + u lattice Boltzmann step on GB300.
+
+Default workload: the 3D single-crystal configuration, 256^3 periodic,
+D3Q15 (phi) / D3Q7 (u), FP32, <100> anisotropy eps = 0.05, Delta = 0.3,
+centred seed of radius 8 (Younsi & Cartalade's 3D parameter set, Sec. 5.2).
+A step is one time step of the whole domain; the metric is MLUPS (million
+lattice-site updates per second) with the fraction of the measured HBM copy
+bandwidth that the step kernel's algorithmic bytes reach.
+
+Under torchrun every rank advances its own independent domain (replicas of
+the workload; weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle (the method written plainly from
+the paper) on the host cores: each step is one oracle time step of a 64^3
+periodic crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, lattice, precision, n)
+    "c2-256-fp32": ("3D single crystal 256^3 periodic, D3Q15/D3Q7, FP32, <100> eps=0.05, Delta=0.3, seed R=8", 1, 1, 256),
+    "c3-512-fp16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with FP16 deviation storage, "
+                       "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 2, 512),
+    "c3-512-bf16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with BF16 deviation storage, "
+                       "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 3, 512),
+    "c3-512-fp32": ("3D 512^3 periodic, D3Q15/D3Q7, FP32, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 1, 512),
+}
+DTYPE = {0: "f64", 1: "f32", 2: "f32 arithmetic, f16 storage", 3: "f32 arithmetic, bf16 storage"}
+METRIC = "fused phi+u LB step MLUPS"
+KERNEL_SOURCES = ["step_kernel.cuh", "lbpf_internal.cuh"]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1606_09432_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    or None when there is none or the kernel changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    info = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            info[k.strip()] = v.strip().strip("`")
+    if info.get("kernel_source_hash") != kernel_hash():
+        return None
+    try:
+        return float(info["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_solver(L, W, workload, stream):
+    desc, lattice, precision, n = WORKLOADS[workload]
+    w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
+    prm = dict(w["params"])
+    lam = prm.pop("lam")
+    dom = L.make_domain(n, n, n, lam=lam, crystals=[L.make_crystal(**w["aniso"])], **prm)
+    s = L.Solver(dom, lattice, L.LBPF_GRAD_DD, precision, stream=stream)
+    s.seed(w["seeds"])
+    return s, w
+
+
+def cpu_oracle_rate(workload: str, budget_s: float, n: int = 64, max_steps: int | None = None):
+    """Oracle MLUPS on a periodic n^3 crop of the workload (host cores)."""
+    from oracle import oracle as O
+    from paper_1606_09432_gb300 import workloads as W
+    O.build()
+    desc, lattice, precision, _ = WORKLOADS[workload]
+    w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
+    prm = dict(w["params"])
+    lam = prm.pop("lam")
+    p = O.make_params(lattice, n, n, n, lam=lam, crystals=[O.make_crystal(**w["aniso"])], **prm)
+    o = O.Oracle(p).seed([list(s) for s in w["seeds"]])
+    o.step(1)  # warm
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    return n ** 3 * steps / el / 1e6, steps, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1606_09432_gb300 import workloads as W
+    O.build()
+    desc, lattice, precision, _ = WORKLOADS[args.workload]
+    n = 64
+    w = W.c2(n) if args.workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
+    prm = dict(w["params"])
+    lam = prm.pop("lam")
+    p = O.make_params(lattice, n, n, n, lam=lam, crystals=[O.make_crystal(**w["aniso"])], **prm)
+    o = O.Oracle(p).seed([list(s) for s in w["seeds"]])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = n ** 3 * args.steps / el / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "oracle_sample": f"{n}^3 periodic crop, one oracle step per bench step"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{n}^3 crop of the workload, {args.steps} steps"},
+        "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c2-256-fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1606_09432_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_1606_09432_gb300 import lbpf as L
+    from paper_1606_09432_gb300 import workloads as W
+
+    stream = torch.cuda.Stream()
+    desc, lattice, precision, n = WORKLOADS[args.workload]
+    with torch.cuda.stream(stream):
+        s, w = make_solver(L, W, args.workload, stream.cuda_stream)
+    sites = s.query(L.LBPF_Q_SITES)
+    bps = s.query(L.LBPF_Q_BYTES_PER_SITE)
+
+    # warm-up, then K timed steps with an event pair around every launch
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    k0 = s.query(L.LBPF_Q_STEP_KERNELS)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for k in range(args.steps):
+            s.step(1)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    launches = int(s.query(L.LBPF_Q_STEP_KERNELS) - k0)
+    per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])  # ms
+    total_ms = float(ev[0].elapsed_time(ev[-1]))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+    tip, sf, cons = s.measure(*w["centre"])
+
+    # end to end through the public API with host buffers: write the initial
+    # fields from pinned host memory, advance K steps, read phi and u back.
+    e2e = None
+    if True:
+        shape = s.shape()
+        tdt = torch.float64 if precision == L.LBPF_FP64 else torch.float32
+        phi_h = torch.empty(shape, dtype=tdt).pin_memory()
+        u_h = torch.empty(shape, dtype=tdt).pin_memory()
+        L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_PHI, phi_h)
+        L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_U, u_h)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        L.lbpf_write_fields(s.ctx, 0, phi_h, u_h)
+        s.step(args.steps)
+        L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_PHI, phi_h)
+        L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_U, u_h)
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nb = phi_h.numel() * phi_h.element_size()
+        e2e = {"value": round(world * sites * args.steps / el / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(2 * nb / args.steps, 1), "d2h_bytes_per_step": round(2 * nb / args.steps, 1),
+               "note": f"write_fields from pinned host + {args.steps} steps + read phi,u to pinned host"}
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    avg_kernel_s = float(per.mean()) * 1e-3
+    achieved = bps * sites / avg_kernel_s / 1e9
+    traffic = profiled_traffic(args.workload)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, st, el = cpu_oracle_rate(args.workload, args.cpu_budget, n=96)
+        cpu = {"value": round(v, 3), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"96^3 periodic crop of the workload, {st} FP64 oracle steps in {el:.1f} s"}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[precision], "data": "synthetic",
+        "config": {"workload": desc, "sites_per_gpu": int(sites), "parallelism": f"replicas x{world}",
+                   "l2": f"state {s.query(L.LBPF_Q_DEVICE_BYTES) / 1e9:.2f} GB per GPU, larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "step_kernel", "bytes_per_site": bps,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6.8 TB/s"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "check": {"tip_x": round(float(tip[0]), 4), "solid_fraction": sf, "conserved": cons},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

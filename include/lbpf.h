@@ -1,0 +1,232 @@
+/*
+ * lbpf — lattice Boltzmann phase-field crystal growth on one NVIDIA GB300.
+ *
+ * C ABI of the per-time-step update of the phase field phi and the
+ * dimensionless temperature u of a pure substance, as defined by
+ * Younsi & Cartalade, "On anisotropy function in crystal growth simulations
+ * using Lattice Boltzmann equation" (arXiv:1606.09432):
+ *   - model:  Eq. (PhaseField_KarmaRappel), Eq. (Temp_Ramirez), Eq. (TermesAnisotropes)
+ *   - heat LB scheme (Sec. 3.1):  Eqs. (LBE_Eq_Temp)-(ThermalDiffusivity)
+ *   - phase-field LB scheme (Sec. 3.2): Eqs. (LBE_Eq_Phase), (Feq_Phase),
+ *     (Def_M0_Phi)-(LBE_RelaxationTime)
+ *   - lattices (Sec. 3.3, Table 1), gradients (Sec. 4.2),
+ *     anisotropy functions (Secs. 2, 4.1, 4.3, 5.2).
+ *
+ * Conventions for every function:
+ *   - The return value is an lbpf_status; nothing throws or aborts across the
+ *     ABI.  On failure lbpf_last_error() describes the cause.
+ *   - All sizes, positions and radii are in lattice units (sites); physical
+ *     parameters (dx, dt, W0, tau0, kappa) are in any consistent unit system.
+ *   - Fields are row-major with x fastest: element (x, y, z) of a domain of
+ *     size nx*ny*nz is at index (z*ny + y)*nx + x.  Fields read back are
+ *     double for LBPF_FP64 and float for the other precisions; the crystal
+ *     index field is int32.
+ *   - The caller owns every array it passes; inputs are copied during the
+ *     call.  The context owns all device memory it allocates and borrows the
+ *     CUDA stream given to lbpf_create (NULL = the legacy default stream).
+ *   - Calls on one context must not overlap (one host thread at a time).
+ *   - Boundaries are periodic in every direction (the paper's own runs use
+ *     zero-flux bounce-back walls, Sec. 3.3; not provided by this library).
+ */
+#ifndef LBPF_H
+#define LBPF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbpf_ctx lbpf_ctx;
+
+typedef enum {
+    LBPF_OK = 0,
+    LBPF_EINVAL = -1,     /* invalid argument or parameter combination         */
+    LBPF_ENOMEM = -2,     /* device or host allocation failed                  */
+    LBPF_ECUDA = -3,      /* a CUDA runtime call failed (see lbpf_last_error)  */
+    LBPF_ETIMEOUT = -4,   /* reserved: a bounded device wait gave up           */
+    LBPF_ENONFINITE = -5, /* a measurement found NaN or Inf in phi or u        */
+    LBPF_ERANGE = -6      /* output buffer too small                           */
+} lbpf_status;
+
+/* Lattice pairs (Sec. 3.3): phase-field lattice / temperature lattice.
+ * D2Q9/D2Q5 and D3Q15/D3Q7 are the paper's (Table 1); D3Q19 and D3Q27 are
+ * mentioned by the paper (Sec. 3.3) with the standard weights
+ * (1/3, 1/18, 1/36) and (8/27, 2/27, 1/54, 1/216), e^2 = 1/3. */
+typedef enum {
+    LBPF_D2Q9_D2Q5 = 0,
+    LBPF_D3Q15_D3Q7 = 1,
+    LBPF_D3Q19_D3Q7 = 2,
+    LBPF_D3Q27_D3Q7 = 3
+} lbpf_lattice;
+
+/* Gradient of phi (Sec. 4.2): directional derivatives, Eqs.
+ * (Def_DeriveeDirectionnelle) and (Grad_DF-Centree), or central finite
+ * differences along the axes. */
+typedef enum { LBPF_GRAD_DD = 0, LBPF_GRAD_FD = 1 } lbpf_grad;
+
+/* Arithmetic and storage.
+ *   LBPF_FP64:         FP64 arithmetic, FP64 populations.
+ *   LBPF_FP32:         FP32 arithmetic, FP32 populations.
+ *   LBPF_FP32_FP16DEV: FP32 arithmetic; populations stored as FP16
+ *                      deviations g_i - w_i phi and f_i - w_i u for i >= 1
+ *                      (the rest population is rebuilt so that the sums
+ *                      phi = sum g_i, u = sum f_i hold exactly).
+ *   LBPF_FP32_BF16DEV: as above with BF16 deviations. */
+typedef enum {
+    LBPF_FP64 = 0,
+    LBPF_FP32 = 1,
+    LBPF_FP32_FP16DEV = 2,
+    LBPF_FP32_BF16DEV = 3
+} lbpf_precision;
+
+/* Anisotropy functions a_s(n), n = -grad(phi)/|grad(phi)|, Eq. (Def_Normal_Vector).
+ *   LBPF_AS_CUBIC100: 1 - 3 eps + 4 eps sum_a n_a^4, Eq. (As_Function_Classical)
+ *   LBPF_AS_ANGLE:    1 + eps cos(q (varphi - phi0)), varphi = atan2(n_y, n_x),
+ *                     Eq. (As_Theta); 2D lattices only
+ *   LBPF_AS_Y66:      1 + eps (nx^6 - 15 nx^4 ny^2 + 15 nx^2 ny^4 - ny^6), Eq. (As_Y66)
+ *   LBPF_AS_HOYT110:  1 + eps (Q - 3/5) + gamma (3 Q + 66 S - 17/7), Eq. (As_MatSci),
+ *                     Q = sum n_a^4, S = nx^2 ny^2 nz^2
+ *   LBPF_AS_S111:     1 + 66 gamma S.  Eq. (As_Function_S) prints 66 gamma S,
+ *                     which vanishes on the axes; the constant term 1 is
+ *                     added so that Eq. (LBE_Eq_Phase) stays defined. */
+typedef enum {
+    LBPF_AS_CUBIC100 = 0,
+    LBPF_AS_ANGLE = 1,
+    LBPF_AS_Y66 = 2,
+    LBPF_AS_HOYT110 = 3,
+    LBPF_AS_S111 = 4
+} lbpf_aniso;
+
+typedef struct {
+    int kind;     /* lbpf_aniso                                  */
+    double eps;   /* anisotropy strength eps_s                   */
+    double gamma; /* <110>/<111> strength (HOYT110, S111)        */
+    int q;        /* mode of the angle form (ANGLE)              */
+    double phi0;  /* reference angle of the angle form, radians  */
+} lbpf_crystal;
+
+#define LBPF_MAX_CRYSTALS 16
+
+/* One periodic domain and its model parameters (Sec. 2, Sec. 3). */
+typedef struct {
+    int nx, ny, nz;  /* sites; nz = 1 for 2D lattices; each >= 2 in 3D, nx, ny >= 2 */
+    double dx, dt;   /* space and time steps                                       */
+    double W0, tau0; /* interface thickness and kinetic time, Eq. (PhaseField_KarmaRappel) */
+    double kappa;    /* thermal diffusivity, Eq. (Temp_Ramirez)                    */
+    double lambda;   /* coupling constant; <= 0 selects lambda* = kappa tau0/(a2 W0^2),
+                        a2 = 0.6267, which cancels the kinetic coefficient of
+                        Eq. (Kinetic-Coeff)                                        */
+    double delta;    /* undercooling: u(x, 0) = -delta, Eq. (Intial-Cond_u)        */
+    double xi;       /* index-field threshold on |grad phi| (physical units), Sec. 4.3 */
+    int n_crystals;  /* 1..LBPF_MAX_CRYSTALS.  With one crystal its a_s applies
+                        everywhere; with several, the crystal-index field of
+                        Sec. 4.3 / Eq. (As_Multi) selects it per site          */
+    lbpf_crystal crystals[LBPF_MAX_CRYSTALS];
+} lbpf_domain;
+
+/* A diffuse spherical (circular in 2D) nucleus, Eq. (Initial_Condition). */
+typedef struct {
+    double x, y, z; /* centre, lattice units (z ignored in 2D)   */
+    double radius;  /* R_s, lattice units                        */
+    int crystal;    /* 0 .. n_crystals - 1                       */
+} lbpf_seed_t;
+
+/* Create a context holding n_domains independent periodic domains that all
+ * use one lattice pair, gradient operator and precision.  Allocates the
+ * device state of every domain (two population sets per lattice, phi, an
+ * auxiliary heat field, the index field when n_crystals > 1).
+ * domains: n_domains entries (host memory, copied).  stream: a cudaStream_t
+ * or NULL.  On success *out receives the context.
+ * Errors: LBPF_EINVAL (bad sizes or parameters, e.g. the angle form on a 3D
+ * lattice, a non-positive dx/dt/W0/tau0/kappa, relaxation rates <= 1/2),
+ * LBPF_ENOMEM, LBPF_ECUDA. */
+int lbpf_create(const lbpf_domain* domains, int n_domains, int lattice, int grad, int precision,
+                void* stream, lbpf_ctx** out);
+
+/* Initial condition of one domain from seeds, Eqs. (Initial_Condition) and
+ * (Intial-Cond_u): phi = max over seeds of tanh((R - d) dx / (sqrt(2) W0)),
+ * d the periodic (minimum-image) distance to the seed centre; u = -delta; the
+ * index field takes the crystal of the dominant seed where phi > 0 or
+ * |grad phi| > xi, else 0; populations start at their equilibria
+ * g_i = g_i^(0)(phi, N) of Eq. (Feq_Phase) and f_i = w_i u of Eq.
+ * (EqFunction_Tempr).  Resets the step counter.  seeds: host memory.
+ * Errors: LBPF_EINVAL (domain index, n_seeds < 1 or > 4096, crystal out of range). */
+int lbpf_seed(lbpf_ctx* ctx, int domain, const lbpf_seed_t* seeds, int n_seeds);
+
+/* Initial condition from given fields: phi and u (double for LBPF_FP64,
+ * float otherwise; nx*ny*nz elements each) and, when the domain has several
+ * crystals, the int32 index field (NULL: all zero).  Populations start at
+ * equilibrium as in lbpf_seed.  on_device != 0: the pointers are device
+ * memory of the context's GPU, else host memory.  Resets the step counter. */
+int lbpf_write_fields(lbpf_ctx* ctx, int domain, const void* phi, const void* u, const int* index,
+                      int on_device);
+
+/* Advance every domain by n_steps time steps (n_steps >= 0).  One step is
+ * the phase-field scheme of Sec. 3.2 followed by the heat scheme of Sec. 3.1
+ * with Q_u = (phi(t + dt) - phi(t)) / (2 dt).  Asynchronous on the
+ * context's stream; launch errors are returned, device errors surface at the
+ * next synchronising call. */
+int lbpf_step(lbpf_ctx* ctx, int n_steps);
+
+typedef enum {
+    LBPF_FIELD_PHI = 0,   /* phi, Eq. (Def_M0_Phi)                          */
+    LBPF_FIELD_U = 1,     /* u, Eq. (Temperature_LB)                        */
+    LBPF_FIELD_INDEX = 2  /* crystal index I (int32), Sec. 4.3; all 1 with one crystal */
+} lbpf_field;
+
+/* Copy one field of one domain to out (device memory of the context's GPU if
+ * out_on_device != 0, else host memory).  out_bytes must be at least
+ * nx*ny*nz * element size.  Synchronises the stream.
+ * Errors: LBPF_ERANGE (buffer too small), LBPF_EINVAL, LBPF_ECUDA. */
+int lbpf_read_field(lbpf_ctx* ctx, int domain, int field, void* out, int out_on_device,
+                    size_t out_bytes);
+
+/* Copy the populations of one domain, decoded to the arithmetic type
+ * (double for LBPF_FP64, float otherwise): which = 0 for g_i (phase field,
+ * Q_phi arrays of nx*ny*nz), which = 1 for f_i (temperature, Q_u arrays).
+ * Population i of site k is at [i * nx*ny*nz + k]; direction numbering as in
+ * Sec. 3.3 (D3Q19/D3Q27: axes, then the xy-, xz-, yz-edges, then corners).
+ * Synchronises the stream. */
+int lbpf_read_populations(lbpf_ctx* ctx, int domain, int which, void* out, int out_on_device,
+                          size_t out_bytes);
+
+/* Measurements of one domain (synchronises the stream):
+ *   tip6[6]:  distance from the site (cx, cy, cz) to the outermost phi = 0
+ *             crossing along +x, -x, +y, -y, +z, -z (linear interpolation,
+ *             rays of half the domain length; -1 when a ray has no crossing;
+ *             the z entries are -1 in 2D).  The paper defines the tip velocity
+ *             V_p from the tip position (Sec. 3.4) but not the position itself.
+ *   solid_fraction: mean of (1 + phi)/2.
+ *   conserved: sum over sites of (u - phi/2), accumulated in FP64; constant
+ *             on a periodic box (integral of Eq. (Temp_Ramirez)).
+ * Any output pointer may be NULL.  Returns LBPF_ENONFINITE if phi or u holds
+ * a NaN or Inf. */
+int lbpf_measure(lbpf_ctx* ctx, int domain, int cx, int cy, int cz, double* tip6,
+                 double* solid_fraction, double* conserved);
+
+typedef enum {
+    LBPF_Q_SITES = 0,          /* total sites over all domains                       */
+    LBPF_Q_STEPS = 1,          /* steps done since the last seed / write_fields      */
+    LBPF_Q_BYTES_PER_SITE = 2, /* algorithmic HBM bytes one fused step moves per site */
+    LBPF_Q_DEVICE_BYTES = 3,   /* device memory held by the context                  */
+    LBPF_Q_LAMBDA = 4,         /* lambda of domain 0 (after the lambda* rule)        */
+    LBPF_Q_STEP_KERNELS = 5    /* kernel launches issued by lbpf_step so far          */
+} lbpf_query_t;
+
+/* Read a property of the context into *value. */
+int lbpf_query(const lbpf_ctx* ctx, int what, double* value);
+
+/* Release every resource of the context (NULL is accepted).  Synchronises
+ * the stream first. */
+int lbpf_destroy(lbpf_ctx* ctx);
+
+/* Description of the last error on ctx, or of the last error of the calling
+ * thread when ctx is NULL (e.g. after a failed lbpf_create).  Never NULL. */
+const char* lbpf_last_error(const lbpf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBPF_H */

@@ -14,13 +14,14 @@ from __future__ import annotations
 import ctypes as C
 import math
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbpf_oracle.c")
-_LIB = os.path.join(_HERE, "liborc.so")
+_LIB = os.path.join(_HERE, f"liborc.{platform.machine()}.so")
 
 MAXC = 16
 

@@ -1,0 +1,281 @@
+// Per-lattice kernels around the fused step: equilibrium initial
+// populations, the heat update that brings a lagged state up to date, and
+// decoding reads.  Each is one thread per site with periodic wrap; none of
+// them is on the per-step path.
+#pragma once
+
+#include "step_kernel.cuh"
+
+namespace lbpf {
+
+struct SiteNb {
+    long long oxm, oxp, oym, oyp, ozm, ozp;
+    __device__ __forceinline__ long long off(int ex, int ey, int ez) const
+    {
+        return (ex < 0 ? oxm : (ex > 0 ? oxp : 0)) + (ey < 0 ? oym : (ey > 0 ? oyp : 0)) +
+               (ez < 0 ? ozm : (ez > 0 ? ozp : 0));
+    }
+};
+
+__device__ __forceinline__ SiteNb site_nb(const DomainDev& d, long long s, int& x, int& y, int& z)
+{
+    const long long nxy = (long long)d.nx * d.ny;
+    z = (int)(s / nxy);
+    const long long r = s - (long long)z * nxy;
+    y = (int)(r / d.nx);
+    x = (int)(r - (long long)y * d.nx);
+    SiteNb nb;
+    nb.oxm = (x == 0) ? d.nx - 1 : -1;
+    nb.oxp = (x == d.nx - 1) ? -(d.nx - 1) : 1;
+    nb.oym = (long long)((y == 0) ? d.ny - 1 : -1) * d.nx;
+    nb.oyp = (long long)((y == d.ny - 1) ? -(d.ny - 1) : 1) * d.nx;
+    nb.ozm = (d.nz == 1) ? 0 : (long long)((z == 0) ? d.nz - 1 : -1) * nxy;
+    nb.ozp = (d.nz == 1) ? 0 : (long long)((z == d.nz - 1) ? -(d.nz - 1) : 1) * nxy;
+    return nb;
+}
+
+// Gradient of phi at site s in lattice units (Sec. 4.2), global-memory stencil.
+template <class PL, class R>
+__device__ __forceinline__ void site_gradient(const R* phi, long long s, const SiteNb& nb, int grad, R& Gx, R& Gy,
+                                              R& Gz)
+{
+    Gx = Gy = Gz = R(0);
+    if (grad == LBPF_GRAD_DD) {
+#pragma unroll
+        for (int i = 1; i < PL::Q; ++i) {
+            const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
+            const R wd = R(PL::w(i)) * (phi[s + nb.off(ex, ey, ez)] - phi[s + nb.off(-ex, -ey, -ez)]);
+            if (ex) Gx += R(ex) * wd;
+            if (ey) Gy += R(ey) * wd;
+            if (ez) Gz += R(ez) * wd;
+        }
+        const R k = R(0.5 / PL::E2);
+        Gx *= k;
+        Gy *= k;
+        Gz *= k;
+    } else {
+        Gx = R(0.5) * (phi[s + nb.oxp] - phi[s + nb.oxm]);
+        Gy = R(0.5) * (phi[s + nb.oyp] - phi[s + nb.oym]);
+        if (PL::D == 3) Gz = R(0.5) * (phi[s + nb.ozp] - phi[s + nb.ozm]);
+    }
+}
+
+// Equilibrium populations from phi (phi[cur]) and u (held in aux[acur]):
+// g_i = g_i^(0)(phi, N), Eq. (Feq_Phase); f_i = w_i u, Eq. (EqFunction_Tempr).
+// finalize_index: the seeded index keeps its value only where phi > 0 or
+// |grad phi| > xi.  Leaves a synchronised state; aux becomes C = u - phi/2 in
+// deviation storage (full storage does not use aux in that state).
+template <class PL, class UL, class S>
+__global__ void equilibrate_kernel(const DomainDev* dp, int cur, int fcur, int acur, int grad, int finalize_index)
+{
+    using R = typename S::Real;
+    using T = typename S::T;
+    const DomainDev& d = *dp;
+    const long long n = d.n;
+    const R* phi = static_cast<const R*>(d.phi[cur]);
+    R* aux = static_cast<R*>(d.aux[acur]);
+    T* g = static_cast<T*>(d.g[cur]);
+    T* f = static_cast<T*>(d.f[fcur]);
+    int8_t* I = d.I[cur];
+    const R De2 = R(d.Dphi / PL::E2);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        const SiteNb nb = site_nb(d, s, x, y, z);
+        R Gx, Gy, Gz;
+        site_gradient<PL, R>(phi, s, nb, grad, Gx, Gy, Gz);
+        const R ph = phi[s];
+        int cryst = 1;
+        if (d.use_index) {
+            int Iv = I[s];
+            if (finalize_index && !(ph > R(0) || Gx * Gx + Gy * Gy + Gz * Gz > R(d.xi_lu * d.xi_lu))) Iv = 0;
+            I[s] = (int8_t)Iv;
+            cryst = Iv;
+        }
+        R a = 1, Nx = 0, Ny = 0, Nz = 0;
+        if (cryst > 0 && cryst <= d.n_crystals) anisotropy<R, PL::D>(d.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
+#pragma unroll
+        for (int i = 0; i < PL::Q; ++i) {
+            const R eN = R(PL::ex(i)) * Nx + R(PL::ey(i)) * Ny + R(PL::ez(i)) * Nz;
+            const R dev = -R(PL::w(i)) * De2 * eN;  // g_i^(0) - w_i phi
+            if (!S::dev)
+                g[(long long)i * n + s] = from_real<T, R>(R(PL::w(i)) * ph + dev);
+            else if (i > 0)
+                g[(long long)(i - 1) * n + s] = from_real<T, R>(dev);
+        }
+        const R u = aux[s];
+#pragma unroll
+        for (int j = 0; j < UL::Q; ++j) {
+            if (!S::dev)
+                f[(long long)j * n + s] = from_real<T, R>(R(UL::w(j)) * u);
+            else if (j > 0)
+                f[(long long)(j - 1) * n + s] = from_real<T, R>(R(0));
+        }
+        if (S::dev) aux[s] = u - R(0.5) * ph;
+    }
+}
+
+// Heat update of step n-1 alone (Eq. LBE_Eq_Temp), lagged -> synchronised:
+// reads f[fcur] (f^{n-1}), aux[acur], phi[cur] (phi^n); writes f[fcur^1]
+// (f^n) and, in deviation storage, aux[acur^1] = C^n.
+template <class PL, class UL, class S>
+__global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acur)
+{
+    using R = typename S::Real;
+    using T = typename S::T;
+    const DomainDev& d = *dp;
+    const long long n = d.n;
+    const R* phi = static_cast<const R*>(d.phi[cur]);
+    const R* auxc = static_cast<const R*>(d.aux[acur]);
+    R* auxn = static_cast<R*>(d.aux[acur ^ 1]);
+    const T* fc = static_cast<const T*>(d.f[fcur]);
+    T* fn = static_cast<T*>(d.f[fcur ^ 1]);
+    const R om = R(1) - R(d.inv_eta_u);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        const SiteNb nb = site_nb(d, s, x, y, z);
+        R fv[UL::Q];
+        R u = 0;
+        R d0 = 0;
+        if (S::dev) {
+#pragma unroll
+            for (int j = 1; j < UL::Q; ++j) d0 -= to_real(fc[(long long)(j - 1) * n + s]);
+        }
+#pragma unroll
+        for (int j = 0; j < UL::Q; ++j) {
+            const long long src = s + nb.off(-UL::ex(j), -UL::ey(j), -UL::ez(j));
+            const R h = auxc[src] + R(0.5) * phi[src];
+            R fj;
+            if (!S::dev)
+                fj = om * to_real(fc[(long long)j * n + src]) + R(UL::w(j)) * h;
+            else
+                fj = R(UL::w(j)) * h + om * ((j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]));
+            fv[j] = fj;
+            u += fj;
+        }
+        if (!S::dev) {
+#pragma unroll
+            for (int j = 0; j < UL::Q; ++j) fn[(long long)j * n + s] = from_real<T, R>(fv[j]);
+        } else {
+#pragma unroll
+            for (int j = 1; j < UL::Q; ++j) fn[(long long)(j - 1) * n + s] = from_real<T, R>(fv[j] - R(UL::w(j)) * u);
+            auxn[s] = u - R(0.5) * phi[s];
+        }
+    }
+}
+
+// u of a synchronised state: Eq. (Temperature_LB).
+template <class PL, class UL, class S>
+__global__ void read_u_kernel(const DomainDev* dp, int cur, int fcur, int acur, typename S::Real* out)
+{
+    using R = typename S::Real;
+    using T = typename S::T;
+    const DomainDev& d = *dp;
+    const long long n = d.n;
+    const T* f = static_cast<const T*>(d.f[fcur]);
+    const R* aux = static_cast<const R*>(d.aux[acur]);
+    const R* phi = static_cast<const R*>(d.phi[cur]);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        if (!S::dev) {
+            R u = 0;
+#pragma unroll
+            for (int j = 0; j < UL::Q; ++j) u += to_real(f[(long long)j * n + s]);
+            out[s] = u;
+        } else {
+            out[s] = aux[s] + R(0.5) * phi[s];
+        }
+    }
+}
+
+// Decoded populations of a synchronised state.
+template <class PL, class UL, class S>
+__global__ void read_pops_kernel(const DomainDev* dp, int which, int cur, int fcur, int acur, typename S::Real* out)
+{
+    using R = typename S::Real;
+    using T = typename S::T;
+    const DomainDev& d = *dp;
+    const long long n = d.n;
+    const int Q = which == 0 ? PL::Q : UL::Q;
+    const T* p = static_cast<const T*>(which == 0 ? d.g[cur] : d.f[fcur]);
+    const R* phi = static_cast<const R*>(d.phi[cur]);
+    const R* aux = static_cast<const R*>(d.aux[acur]);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        if (!S::dev) {
+            for (int i = 0; i < Q; ++i) out[(long long)i * n + s] = to_real(p[(long long)i * n + s]);
+        } else {
+            const R m = which == 0 ? phi[s] : aux[s] + R(0.5) * phi[s];
+            R d0 = 0;
+            for (int i = 1; i < Q; ++i) {
+                const R dv = to_real(p[(long long)(i - 1) * n + s]);
+                const R wi = which == 0 ? R(PL::w(i)) : R(UL::w(i));
+                out[(long long)i * n + s] = wi * m + dv;
+                d0 -= dv;
+            }
+            out[s] = (which == 0 ? R(PL::w(0)) : R(UL::w(0))) * m + d0;
+        }
+    }
+}
+
+inline int grid_for(long long n)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <class PL, class UL, class S>
+struct LauncherImpl {
+    static cudaError_t step(const StepArgs& a, int n_items, size_t smem, cudaStream_t s)
+    {
+        step_kernel<PL, UL, S><<<n_items, NT, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    static size_t smem() { return step_smem_bytes<PL, UL, S>(); }
+    static cudaError_t prepare(size_t bytes)
+    {
+        return cudaFuncSetAttribute(step_kernel<PL, UL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+    static cudaError_t heat_sync(const DomainDev* d, int cur, int fcur, int acur, cudaStream_t s)
+    {
+        heat_sync_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, cur, fcur, acur);
+        return cudaGetLastError();
+    }
+    static cudaError_t equilibrate(const DomainDev* d, int cur, int fcur, int acur, int grad, int finalize,
+                                   cudaStream_t s)
+    {
+        equilibrate_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, cur, fcur, acur, grad, finalize);
+        return cudaGetLastError();
+    }
+    static cudaError_t read_u(const DomainDev* d, int cur, int fcur, int acur, void* out, cudaStream_t s)
+    {
+        read_u_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, cur, fcur, acur, static_cast<typename S::Real*>(out));
+        return cudaGetLastError();
+    }
+    static cudaError_t read_pops(const DomainDev* d, int which, int cur, int fcur, int acur, void* out, cudaStream_t s)
+    {
+        read_pops_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, which, cur, fcur, acur,
+                                                            static_cast<typename S::Real*>(out));
+        return cudaGetLastError();
+    }
+    static const Launchers* get()
+    {
+        static const Launchers L = {&step, &smem, &prepare, &heat_sync, &equilibrate, &read_u, &read_pops, PL::Q, UL::Q, PL::D};
+        return &L;
+    }
+};
+
+template <int LAT>
+const Launchers* launchers_for(int precision)
+{
+    using PL = typename Pair<LAT>::P;
+    using UL = typename Pair<LAT>::U;
+    switch (precision) {
+    case LBPF_FP64: return LauncherImpl<PL, UL, StoreF64>::get();
+    case LBPF_FP32: return LauncherImpl<PL, UL, StoreF32>::get();
+    case LBPF_FP32_FP16DEV: return LauncherImpl<PL, UL, StoreF16>::get();
+    case LBPF_FP32_BF16DEV: return LauncherImpl<PL, UL, StoreB16>::get();
+    default: return nullptr;
+    }
+}
+
+}  // namespace lbpf

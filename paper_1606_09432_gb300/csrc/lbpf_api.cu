@@ -1,0 +1,495 @@
+// Host side of the lbpf C ABI: context, device buffers, launches and the
+// lagged/synchronised state of the heat populations.  See include/lbpf.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbpf_internal.cuh"
+
+using namespace lbpf;
+
+namespace {
+
+thread_local std::string t_err;
+
+// a2 of the thin-interface relations, Eq. (Kinetic-Coeff); lambda* cancels beta.
+constexpr double kA2 = 0.6267;
+
+}  // namespace
+
+struct lbpf_ctx {
+    int lattice = 0, grad = 0, precision = 0, dim = 2;
+    int Qg = 0, Qu = 0, Sg = 0, Su = 0;
+    size_t rsize = 8, ssize = 8;
+    int n_domains = 0;
+    std::vector<lbpf_domain> in;
+    std::vector<DomainDev> dd;
+    DomainDev* d_dd = nullptr;
+    WorkItem* d_items = nullptr;
+    int n_items = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    const Launchers* L = nullptr;
+    size_t smem = 0;
+    int cur = 0, fcur = 0, acur = 0, lagged = 0;
+    long long steps = 0, kernels = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double* red = nullptr;
+    double* d_seeds = nullptr;
+    int seeds_cap = 0;
+    size_t dev_bytes = 0;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+static int fail(lbpf_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        t_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(c, LBPF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static int dev_alloc(lbpf_ctx* c, void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, e == cudaErrorMemoryAllocation ? LBPF_ENOMEM : LBPF_ECUDA, "cudaMalloc(%zu bytes): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    c->dev_bytes += bytes;
+    return LBPF_OK;
+}
+
+static const Launchers* pick(int lattice, int precision)
+{
+    switch (lattice) {
+    case LBPF_D2Q9_D2Q5: return launchers_d2q9(precision);
+    case LBPF_D3Q15_D3Q7: return launchers_d3q15(precision);
+    case LBPF_D3Q19_D3Q7: return launchers_d3q19(precision);
+    case LBPF_D3Q27_D3Q7: return launchers_d3q27(precision);
+    default: return nullptr;
+    }
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static void free_all(lbpf_ctx* c)
+{
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+// Planes per work item along z: enough items to fill the GPU several times
+// over, at least 8 planes each (each item recomputes two halo planes).
+static int choose_zchunk(long long tiles_xy, int nz)
+{
+    const char* env = getenv("LBPF_ZCHUNK");
+    if (env && atoi(env) > 0) return atoi(env) < nz ? atoi(env) : nz;
+    const long long target = 152LL * 4;
+    long long chunks = (target + tiles_xy - 1) / tiles_xy;
+    if (chunks < 1) chunks = 1;
+    long long zc = (nz + chunks - 1) / chunks;
+    if (zc < 8) zc = 8;
+    if (zc > nz) zc = nz;
+    return (int)zc;
+}
+
+extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattice, int grad, int precision,
+                           void* stream, lbpf_ctx** out)
+{
+    lbpf_ctx* c = nullptr;
+    if (!out) return fail(nullptr, LBPF_EINVAL, "lbpf_create: out is NULL");
+    *out = nullptr;
+    if (!domains || n_domains < 1) return fail(nullptr, LBPF_EINVAL, "lbpf_create: need at least one domain");
+    if (grad != LBPF_GRAD_DD && grad != LBPF_GRAD_FD) return fail(nullptr, LBPF_EINVAL, "lbpf_create: bad grad %d", grad);
+    const Launchers* L = pick(lattice, precision);
+    if (!L) return fail(nullptr, LBPF_EINVAL, "lbpf_create: bad lattice %d or precision %d", lattice, precision);
+    const int dim = L->D;
+    for (int k = 0; k < n_domains; ++k) {
+        const lbpf_domain& d = domains[k];
+        if (d.nx < 2 || d.ny < 2 || (dim == 2 && d.nz != 1) || (dim == 3 && d.nz < 2))
+            return fail(nullptr, LBPF_EINVAL, "domain %d: sizes %d x %d x %d invalid for a %dD lattice (each >= 2; nz = 1 in 2D)",
+                        k, d.nx, d.ny, d.nz, dim);
+        if ((long long)d.nx * d.ny > (1LL << 31) || (long long)d.nx * d.ny * d.nz > (1LL << 40))
+            return fail(nullptr, LBPF_EINVAL, "domain %d: too many sites", k);
+        if (!finite_pos(d.dx) || !finite_pos(d.dt) || !finite_pos(d.W0) || !finite_pos(d.tau0) || !finite_pos(d.kappa))
+            return fail(nullptr, LBPF_EINVAL, "domain %d: dx, dt, W0, tau0, kappa must be finite and > 0", k);
+        if (!std::isfinite(d.lambda) || !std::isfinite(d.delta) || !std::isfinite(d.xi) || d.xi < 0)
+            return fail(nullptr, LBPF_EINVAL, "domain %d: lambda, delta, xi must be finite (xi >= 0)", k);
+        if (d.n_crystals < 1 || d.n_crystals > LBPF_MAX_CRYSTALS)
+            return fail(nullptr, LBPF_EINVAL, "domain %d: n_crystals %d not in 1..%d", k, d.n_crystals, LBPF_MAX_CRYSTALS);
+        for (int j = 0; j < d.n_crystals; ++j) {
+            const lbpf_crystal& cr = d.crystals[j];
+            if (cr.kind < LBPF_AS_CUBIC100 || cr.kind > LBPF_AS_S111)
+                return fail(nullptr, LBPF_EINVAL, "domain %d crystal %d: unknown anisotropy kind %d", k, j, cr.kind);
+            if (cr.kind == LBPF_AS_ANGLE && (dim != 2 || cr.q < 1))
+                return fail(nullptr, LBPF_EINVAL, "domain %d crystal %d: the angle form needs a 2D lattice and q >= 1", k, j);
+            if (!std::isfinite(cr.eps) || !std::isfinite(cr.gamma) || !std::isfinite(cr.phi0))
+                return fail(nullptr, LBPF_EINVAL, "domain %d crystal %d: non-finite parameter", k, j);
+        }
+    }
+
+    c = new (std::nothrow) lbpf_ctx();
+    if (!c) return fail(nullptr, LBPF_ENOMEM, "lbpf_create: out of host memory");
+    c->lattice = lattice;
+    c->grad = grad;
+    c->precision = precision;
+    c->dim = dim;
+    c->L = L;
+    c->Qg = L->Qphi;
+    c->Qu = L->Qu;
+    const bool dev = precision == LBPF_FP32_FP16DEV || precision == LBPF_FP32_BF16DEV;
+    c->Sg = dev ? c->Qg - 1 : c->Qg;
+    c->Su = dev ? c->Qu - 1 : c->Qu;
+    c->rsize = precision == LBPF_FP64 ? 8 : 4;
+    c->ssize = precision == LBPF_FP64 ? 8 : (precision == LBPF_FP32 ? 4 : 2);
+    c->n_domains = n_domains;
+    c->in.assign(domains, domains + n_domains);
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, LBPF_ECUDA, "lbpf_create: no CUDA device");
+    }
+    const double e2u = (dim == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
+
+    int rc = LBPF_OK;
+    long long max_n = 0;
+    std::vector<WorkItem> items;
+    c->dd.resize(n_domains);
+    for (int k = 0; k < n_domains && rc == LBPF_OK; ++k) {
+        const lbpf_domain& d = domains[k];
+        DomainDev& h = c->dd[k];
+        memset(&h, 0, sizeof(h));
+        h.nx = d.nx;
+        h.ny = d.ny;
+        h.nz = d.nz;
+        h.n = (long long)d.nx * d.ny * d.nz;
+        max_n = h.n > max_n ? h.n : max_n;
+        // D_phi = (W0^2/tau0)(dt/dx^2), Eq. (LBE_RelaxationTime)
+        h.Dphi = (d.W0 * d.W0 / d.tau0) * (d.dt / (d.dx * d.dx));
+        h.qphi = d.dt / d.tau0;
+        h.lambda = d.lambda > 0.0 ? d.lambda : d.kappa * d.tau0 / (kA2 * d.W0 * d.W0);
+        // kappa = e^2 (eta_u - 1/2) dx^2 / dt, Eq. (ThermalDiffusivity)
+        h.inv_eta_u = 1.0 / (d.kappa * d.dt / (e2u * d.dx * d.dx) + 0.5);
+        h.xi_lu = d.xi * d.dx;
+        h.n_crystals = d.n_crystals;
+        h.use_index = d.n_crystals > 1;
+        for (int j = 0; j < d.n_crystals; ++j) {
+            h.cr[j].kind = d.crystals[j].kind;
+            h.cr[j].q = d.crystals[j].q;
+            h.cr[j].eps = d.crystals[j].eps;
+            h.cr[j].gamma = d.crystals[j].gamma;
+            h.cr[j].phi0 = d.crystals[j].phi0;
+        }
+        for (int b = 0; b < 2 && rc == LBPF_OK; ++b) {
+            rc = dev_alloc(c, &h.g[b], (size_t)c->Sg * h.n * c->ssize);
+            if (rc == LBPF_OK) rc = dev_alloc(c, &h.f[b], (size_t)c->Su * h.n * c->ssize);
+            if (rc == LBPF_OK) rc = dev_alloc(c, &h.phi[b], (size_t)h.n * c->rsize);
+            if (rc == LBPF_OK) rc = dev_alloc(c, &h.aux[b], (size_t)h.n * c->rsize);
+            if (rc == LBPF_OK && h.use_index) rc = dev_alloc(c, reinterpret_cast<void**>(&h.I[b]), (size_t)h.n);
+        }
+        // zero state so that an unseeded domain holds finite values
+        for (int b = 0; b < 2 && rc == LBPF_OK; ++b) {
+            if (cudaMemsetAsync(h.g[b], 0, (size_t)c->Sg * h.n * c->ssize, c->stream) != cudaSuccess ||
+                cudaMemsetAsync(h.f[b], 0, (size_t)c->Su * h.n * c->ssize, c->stream) != cudaSuccess ||
+                cudaMemsetAsync(h.phi[b], 0, (size_t)h.n * c->rsize, c->stream) != cudaSuccess ||
+                cudaMemsetAsync(h.aux[b], 0, (size_t)h.n * c->rsize, c->stream) != cudaSuccess ||
+                (h.use_index && cudaMemsetAsync(h.I[b], 0, (size_t)h.n, c->stream) != cudaSuccess))
+                rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
+        }
+        // work items: TX x TY columns, z split into chunks
+        const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
+        const int zc = dim == 3 ? choose_zchunk((long long)tx * ty, d.nz) : 1;
+        for (int z0 = 0; z0 < d.nz; z0 += zc)
+            for (int by = 0; by < ty; ++by)
+                for (int bx = 0; bx < tx; ++bx) {
+                    WorkItem w;
+                    w.dom = k;
+                    w.x0 = bx * TX;
+                    w.y0 = by * TY;
+                    w.z0 = z0;
+                    w.z1 = z0 + zc < d.nz ? z0 + zc : d.nz;
+                    w.pad = 0;
+                    items.push_back(w);
+                }
+    }
+    if (rc == LBPF_OK) {
+        c->n_items = (int)items.size();
+        rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_items), sizeof(WorkItem) * items.size());
+    }
+    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_dd), sizeof(DomainDev) * n_domains);
+    if (rc == LBPF_OK) {
+        c->scratch_bytes = (size_t)max_n * (c->rsize > 4 ? c->rsize : 4);
+        rc = dev_alloc(c, &c->scratch, c->scratch_bytes);
+    }
+    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), sizeof(double) * (3 * kReduceBlocks + 16));
+    if (rc == LBPF_OK) {
+        if (cudaMemcpyAsync(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomainDev) * n_domains, cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess)
+            rc = fail(c, LBPF_ECUDA, "lbpf_create: copying the domain table failed");
+    }
+    if (rc == LBPF_OK) {
+        c->smem = L->step_smem();
+        cudaError_t e = L->prepare(c->smem);
+        if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
+    }
+    if (rc == LBPF_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
+        rc = fail(c, LBPF_ECUDA, "lbpf_create: stream synchronisation failed");
+    if (rc != LBPF_OK) {
+        t_err = c->err;
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return LBPF_OK;
+}
+
+static int check_ctx(lbpf_ctx* c, int domain)
+{
+    if (!c) return fail(nullptr, LBPF_EINVAL, "context is NULL");
+    if (domain < 0 || domain >= c->n_domains) return fail(c, LBPF_EINVAL, "domain %d out of range", domain);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LBPF_ECUDA, "cudaSetDevice(%d) failed", c->device);
+    return LBPF_OK;
+}
+
+// Lagged -> synchronised: the heat update of the last step on every domain.
+static int sync_state(lbpf_ctx* c)
+{
+    if (!c->lagged) return LBPF_OK;
+    for (int k = 0; k < c->n_domains; ++k) CK(c->L->heat_sync(c->d_dd + k, c->cur, c->fcur, c->acur, c->stream));
+    c->fcur ^= 1;
+    if (c->Sg != c->Qg) c->acur ^= 1;
+    c->lagged = 0;
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_seed(lbpf_ctx* c, int domain, const lbpf_seed_t* seeds, int n_seeds)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    if (!seeds || n_seeds < 1 || n_seeds > 4096) return fail(c, LBPF_EINVAL, "lbpf_seed: need 1..4096 seeds");
+    const lbpf_domain& d = c->in[domain];
+    std::vector<double> h(5 * (size_t)n_seeds);
+    for (int j = 0; j < n_seeds; ++j) {
+        const lbpf_seed_t& s = seeds[j];
+        if (s.crystal < 0 || s.crystal >= d.n_crystals)
+            return fail(c, LBPF_EINVAL, "lbpf_seed: seed %d crystal %d out of range", j, s.crystal);
+        if (!std::isfinite(s.x) || !std::isfinite(s.y) || !std::isfinite(s.z) || !std::isfinite(s.radius))
+            return fail(c, LBPF_EINVAL, "lbpf_seed: seed %d not finite", j);
+        h[5 * j + 0] = s.x;
+        h[5 * j + 1] = s.y;
+        h[5 * j + 2] = s.z;
+        h[5 * j + 3] = s.radius;
+        h[5 * j + 4] = s.crystal;
+    }
+    if ((rc = sync_state(c))) return rc;
+    if (n_seeds > c->seeds_cap) {
+        void* p = nullptr;
+        if ((rc = dev_alloc(c, &p, sizeof(double) * 5 * n_seeds))) return rc;
+        c->d_seeds = static_cast<double*>(p);
+        c->seeds_cap = n_seeds;
+    }
+    CK(cudaMemcpyAsync(c->d_seeds, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_seed(c->d_dd + domain, c->dd[domain].n, c->cur, c->acur, c->precision, c->d_seeds, n_seeds, c->dim,
+                   d.dx / (std::sqrt(2.0) * d.W0), -d.delta, c->stream));
+    CK(c->L->equilibrate(c->d_dd + domain, c->cur, c->fcur, c->acur, c->grad, 1, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->steps = 0;
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_write_fields(lbpf_ctx* c, int domain, const void* phi, const void* u, const int* index,
+                                 int on_device)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    if (!phi || !u) return fail(c, LBPF_EINVAL, "lbpf_write_fields: phi and u are required");
+    if ((rc = sync_state(c))) return rc;
+    const DomainDev& h = c->dd[domain];
+    const size_t bytes = (size_t)h.n * c->rsize;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h.phi[c->cur], phi, bytes, kind, c->stream));
+    CK(cudaMemcpyAsync(h.aux[c->acur], u, bytes, kind, c->stream));
+    if (h.use_index) {
+        if (index) {
+            CK(cudaMemcpyAsync(c->scratch, index, sizeof(int) * h.n, kind, c->stream));
+            CK(launch_index_from_i32(static_cast<const int*>(c->scratch), h.I[c->cur], h.n, h.n_crystals, c->stream));
+        } else {
+            CK(launch_fill_i8(h.I[c->cur], 0, h.n, c->stream));
+        }
+    }
+    CK(c->L->equilibrate(c->d_dd + domain, c->cur, c->fcur, c->acur, c->grad, 0, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->steps = 0;
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_step(lbpf_ctx* c, int n_steps)
+{
+    int rc = check_ctx(c, 0);
+    if (rc) return rc;
+    if (n_steps < 0) return fail(c, LBPF_EINVAL, "lbpf_step: n_steps < 0");
+    for (int k = 0; k < n_steps; ++k) {
+        StepArgs a;
+        a.doms = c->d_dd;
+        a.items = c->d_items;
+        a.cur = c->cur;
+        a.fcur = c->fcur;
+        a.acur = c->acur;
+        a.collide = c->lagged;
+        a.grad = c->grad;
+        CK(c->L->step(a, c->n_items, c->smem, c->stream));
+        c->cur ^= 1;
+        c->acur ^= 1;
+        if (c->lagged) c->fcur ^= 1;
+        c->lagged = 1;
+        c->steps += 1;
+        c->kernels += 1;
+    }
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_read_field(lbpf_ctx* c, int domain, int field, void* out, int out_on_device, size_t out_bytes)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    if (!out) return fail(c, LBPF_EINVAL, "lbpf_read_field: out is NULL");
+    const DomainDev& h = c->dd[domain];
+    const size_t esize = field == LBPF_FIELD_INDEX ? sizeof(int) : c->rsize;
+    const size_t bytes = (size_t)h.n * esize;
+    if (field < LBPF_FIELD_PHI || field > LBPF_FIELD_INDEX) return fail(c, LBPF_EINVAL, "lbpf_read_field: bad field %d", field);
+    if (out_bytes < bytes) return fail(c, LBPF_ERANGE, "lbpf_read_field: need %zu bytes, got %zu", bytes, out_bytes);
+    void* dst = out_on_device ? out : c->scratch;
+    if (field == LBPF_FIELD_PHI) {
+        CK(cudaMemcpyAsync(out, h.phi[c->cur], bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           c->stream));
+    } else {
+        if (field == LBPF_FIELD_U) {
+            if ((rc = sync_state(c))) return rc;
+            CK(c->L->read_u(c->d_dd + domain, c->cur, c->fcur, c->acur, dst, c->stream));
+        } else if (h.use_index) {
+            CK(launch_index_to_i32(h.I[c->cur], static_cast<int*>(dst), h.n, c->stream));
+        } else {
+            // one crystal: index 1 everywhere (staged through the int8 view of scratch)
+            int8_t* tmp = static_cast<int8_t*>(c->scratch) + (size_t)h.n * 3;
+            if (out_on_device) {
+                CK(launch_fill_i8(tmp, 1, h.n, c->stream));
+                CK(launch_index_to_i32(tmp, static_cast<int*>(dst), h.n, c->stream));
+            } else {
+                CK(cudaStreamSynchronize(c->stream));
+                int* o = static_cast<int*>(out);
+                for (long long s = 0; s < h.n; ++s) o[s] = 1;
+                return LBPF_OK;
+            }
+        }
+        if (!out_on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_read_populations(lbpf_ctx* c, int domain, int which, void* out, int out_on_device, size_t out_bytes)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    if (!out || (which != 0 && which != 1)) return fail(c, LBPF_EINVAL, "lbpf_read_populations: bad arguments");
+    const DomainDev& h = c->dd[domain];
+    const int Q = which == 0 ? c->Qg : c->Qu;
+    const size_t bytes = (size_t)Q * h.n * c->rsize;
+    if (out_bytes < bytes) return fail(c, LBPF_ERANGE, "lbpf_read_populations: need %zu bytes, got %zu", bytes, out_bytes);
+    if ((rc = sync_state(c))) return rc;
+    void* dst = out;
+    if (!out_on_device) CK(cudaMalloc(&dst, bytes));
+    cudaError_t e = c->L->read_pops(c->d_dd + domain, which, c->cur, c->fcur, c->acur, dst, c->stream);
+    if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (!out_on_device) cudaFree(dst);
+    if (e != cudaSuccess) return fail(c, LBPF_ECUDA, "lbpf_read_populations: %s", cudaGetErrorString(e));
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, double* tip6, double* solid_fraction,
+                            double* conserved)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    const DomainDev& h = c->dd[domain];
+    if (cx < 0 || cx >= h.nx || cy < 0 || cy >= h.ny || cz < 0 || cz >= h.nz)
+        return fail(c, LBPF_EINVAL, "lbpf_measure: centre (%d, %d, %d) outside the domain", cx, cy, cz);
+    if ((rc = sync_state(c))) return rc;
+    CK(c->L->read_u(c->d_dd + domain, c->cur, c->fcur, c->acur, c->scratch, c->stream));
+    double* outp = c->red + 3 * kReduceBlocks;
+    CK(launch_reduce(h.phi[c->cur], c->scratch, h.n, c->precision, c->red, outp, c->stream));
+    CK(launch_tips(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, c->dim, c->precision, outp + 3, c->stream));
+    double hv[9];
+    CK(cudaMemcpyAsync(hv, outp, sizeof(hv), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (tip6)
+        for (int k = 0; k < 6; ++k) tip6[k] = hv[3 + k];
+    if (solid_fraction) *solid_fraction = hv[0] / (double)h.n;
+    if (conserved) *conserved = hv[1];
+    if (hv[2] > 0) return fail(c, LBPF_ENONFINITE, "lbpf_measure: %.0f non-finite values in phi or u", hv[2]);
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_query(const lbpf_ctx* c, int what, double* value)
+{
+    if (!c || !value) return fail(nullptr, LBPF_EINVAL, "lbpf_query: NULL argument");
+    double v = 0;
+    switch (what) {
+    case LBPF_Q_SITES:
+        for (const DomainDev& h : c->dd) v += (double)h.n;
+        break;
+    case LBPF_Q_STEPS: v = (double)c->steps; break;
+    case LBPF_Q_BYTES_PER_SITE: {
+        // read + write of every stored population, of phi and of aux (and of
+        // the index field when it is used)
+        v = 2.0 * (c->Sg + c->Su) * c->ssize + 4.0 * c->rsize;
+        if (c->dd[0].use_index) v += 2.0;
+        break;
+    }
+    case LBPF_Q_DEVICE_BYTES: v = (double)c->dev_bytes; break;
+    case LBPF_Q_LAMBDA: v = c->dd[0].lambda; break;
+    case LBPF_Q_STEP_KERNELS: v = (double)c->kernels; break;
+    default: return fail(const_cast<lbpf_ctx*>(c), LBPF_EINVAL, "lbpf_query: unknown property %d", what);
+    }
+    *value = v;
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_destroy(lbpf_ctx* c)
+{
+    if (!c) return LBPF_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return LBPF_OK;
+}
+
+extern "C" const char* lbpf_last_error(const lbpf_ctx* c) { return c ? c->err.c_str() : t_err.c_str(); }

@@ -1,0 +1,364 @@
+// Fused time step of the phase-field and heat lattice Boltzmann schemes
+// (Younsi & Cartalade, arXiv:1606.09432, Secs. 3.1-3.2), one launch per step.
+//
+// State at the start of step n (the "lagged" state):
+//   g^n (phase-field populations), phi^n (its zeroth moment, Eq. Def_M0_Phi),
+//   f^{n-1} (temperature populations one step behind) and the auxiliary field
+//     full storage:      aux = psi^{n-1} = u^{n-1} / eta_u - phi^{n-1} / 2
+//     deviation storage: aux = C^{n-1}   = u^{n-1} - phi^{n-1} / 2
+// One launch produces g^{n+1}, phi^{n+1}, f^n and aux^n.  The heat update of
+// step n-1 (Eq. LBE_Eq_Temp with Q_u = (phi^n - phi^{n-1}) / (2 dt), Sec. 3.1)
+// is done inside the launch of step n, because the phase-field update of step
+// n needs u^n on the neighbours of each site (Q_phi at x - e_i in pull form),
+// and u^n in turn needs phi^n, which the previous launch produced.  The
+// collision arithmetic is that of the paper; only the launch boundary moves.
+// A "load" launch starts from a synchronised state (f^n, u^n known): it skips
+// the heat collision and only reads u^n.
+//
+// Phase-field update in pull form (Eq. LBE_Eq_Phase), destination y,
+// source x = y - e_i:
+//   g_i^{n+1}(y) = c1(x) g_i^n(x) - c2(x) g_i^n(y) + w_i (s(x) + e_i . v(x))
+//   c1 = (1 - 1/eta_phi) / a_s^2,  c2 = (1 - a_s^2) / a_s^2,
+//   s  = (phi / eta_phi + (dt/tau0) Q_phi) / a_s^2,
+//   v  = -D_phi N / (e^2 eta_phi a_s^2),   D_phi = (W0^2/tau0)(dt/dx^2),
+// which is Eq. (LBE_Eq_Phase) divided by a_s^2(x) with g^(0) of Eq.
+// (Feq_Phase), eta_phi of Eq. (LBE_RelaxationTime) and Q_phi of Eq.
+// (LBE_SourceTerm), all evaluated at the collision node x.
+//
+// Tiling: a block owns a TX x TY column of sites and marches along z over
+// [z0, z1), keeping rings of planes in shared memory: phi^n and
+// h = aux + phi^n / 2 on the tile plus a 2-site halo, and the collision
+// coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
+// is read from HBM once per launch except the halo rims, which neighbouring
+// blocks share through L2.
+#pragma once
+
+#include "lbpf_internal.cuh"
+
+namespace lbpf {
+
+template <class PL, class UL, class S>
+__global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
+{
+    using R = typename S::Real;
+    using T = typename S::T;
+    constexpr int D = PL::D;
+    constexpr int RX = TX + 4, RY = TY + 4, RP = RX * RY;  // tile + 2-site halo
+    constexpr int CX = TX + 2, CY = TY + 2, CP = CX * CY;  // tile + 1-site halo
+    constexpr int NPH = D == 3 ? 4 : 1;                     // phi / index ring depth
+    constexpr int NH = D == 3 ? 3 : 1;                      // h ring depth
+    constexpr int NC = D == 3 ? 3 : 1;                      // coefficient ring depth
+    constexpr int NCO = D + 3;                              // c1, c2, s, v[D]
+    constexpr int QG = PL::Q, QU = UL::Q;
+    constexpr bool DEV = S::dev;
+    (void)RY;
+    (void)CY;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* s_phi = reinterpret_cast<R*>(smem_raw);
+    R* s_h = s_phi + NPH * RP;
+    R* s_co = s_h + NH * RP;
+    int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * NCO * CP);
+
+    const WorkItem it = args.items[blockIdx.x];
+    const DomainDev& dm = args.doms[it.dom];
+    const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
+    const long long n = dm.n;
+    const long long nxy = (long long)nx * ny;
+    const int x0 = it.x0, y0 = it.y0;
+    const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
+    const int tid = threadIdx.x;
+    const bool collide = args.collide != 0;
+    const bool use_index = dm.use_index != 0;
+    const bool need_h = collide || DEV;
+
+    const T* __restrict__ gc = static_cast<const T*>(dm.g[args.cur]);
+    T* __restrict__ gn = static_cast<T*>(dm.g[args.cur ^ 1]);
+    const R* __restrict__ phic = static_cast<const R*>(dm.phi[args.cur]);
+    R* __restrict__ phin = static_cast<R*>(dm.phi[args.cur ^ 1]);
+    const T* __restrict__ fc = static_cast<const T*>(dm.f[args.fcur]);
+    T* __restrict__ fn = static_cast<T*>(dm.f[args.fcur ^ 1]);
+    const R* __restrict__ auxc = static_cast<const R*>(dm.aux[args.acur]);
+    R* __restrict__ auxn = static_cast<R*>(dm.aux[args.acur ^ 1]);
+    const int8_t* __restrict__ Ic = dm.I[args.cur];
+    int8_t* __restrict__ In = dm.I[args.cur ^ 1];
+
+    const R Dphi = R(dm.Dphi);
+    const R De2 = R(dm.Dphi / PL::E2);
+    const R qphi = R(dm.qphi);
+    const R lam = R(dm.lambda);
+    const R ieu = R(dm.inv_eta_u);
+    const R om_u = R(1) - ieu;
+    const R xi2 = R(dm.xi_lu * dm.xi_lu);
+    (void)Dphi;
+
+    auto wrapx = [&](int v) { return v < 0 ? v + nx : (v >= nx ? v - nx : v); };
+    auto wrapy = [&](int v) { return v < 0 ? v + ny : (v >= ny ? v - ny : v); };
+    auto wrapz = [&](int v) { return v < 0 ? v + nz : (v >= nz ? v - nz : v); };
+    auto sphi = [&](int zp) { return zp & (NPH - 1); };
+    auto sh = [&](int zp) { return (zp + 3) % NH; };
+    auto sco = [&](int zp) { return (zp + 3) % NC; };
+
+    // -- load one plane of phi^n (and h, I) on the tile + 2-site halo ---------
+    auto load_plane = [&](int zp) {
+        const long long zo = (long long)wrapz(zp) * nxy;
+        R* dphi = s_phi + sphi(zp) * RP;
+        R* dh = s_h + sh(zp) * RP;
+        int8_t* dI = s_I + sphi(zp) * RP;
+        const int rows = th + 4;
+        for (int k = tid; k < RX * rows; k += NT) {
+            const int ly = k / RX, lx = k - ly * RX;
+            if (lx >= tw + 4) continue;
+            const long long s = zo + (long long)wrapy(y0 + ly - 2) * nx + wrapx(x0 + lx - 2);
+            const R ph = phic[s];
+            dphi[k] = ph;
+            if (need_h) dh[k] = auxc[s] + R(0.5) * ph;
+            if (use_index) dI[k] = Ic[s];
+        }
+    };
+
+    // -- heat update, gradient, anisotropy, collision coefficients ----------
+    // on one plane of the tile + 1-site halo; heat outputs of the tile
+    // interior are stored when `store` is set.
+    auto coef_plane = [&](int zp, bool store) {
+        const int zw = wrapz(zp);
+        const long long zo = (long long)zw * nxy;
+        const int zm = wrapz(zp - 1), zq = wrapz(zp + 1);
+        const long long ozm = (long long)(zm - zw) * nxy, ozp = (long long)(zq - zw) * nxy;
+        R* dco = s_co + sco(zp) * NCO * CP;
+        const int rows = th + 2;
+        for (int k = tid; k < CX * rows; k += NT) {
+            const int ly = k / CX, lx = k - ly * CX;
+            if (lx >= tw + 2) continue;
+            const int px = lx + 1, py = ly + 1;  // position in the halo-2 frame
+            const int gx = wrapx(x0 + lx - 1), gy = wrapy(y0 + ly - 1);
+            const long long s = zo + (long long)gy * nx + gx;
+            const bool inner = store && lx >= 1 && lx <= tw && ly >= 1 && ly <= th;
+            const R ph = s_phi[sphi(zp) * RP + py * RX + px];
+
+            // offsets of the periodic neighbours of s
+            const int gxm = wrapx(gx - 1), gxp = wrapx(gx + 1);
+            const int gym = wrapy(gy - 1), gyp = wrapy(gy + 1);
+            const long long oxm = gxm - gx, oxp = gxp - gx;
+            const long long oym = (long long)(gym - gy) * nx, oyp = (long long)(gyp - gy) * nx;
+            auto off = [&](int ex, int ey, int ez) -> long long {
+                return (ex < 0 ? oxm : (ex > 0 ? oxp : 0)) + (ey < 0 ? oym : (ey > 0 ? oyp : 0)) +
+                       (D == 3 ? (ez < 0 ? ozm : (ez > 0 ? ozp : 0)) : 0);
+            };
+
+            // u^n at this site
+            R u = 0;
+            if (collide) {
+                R fv[QU];
+                R d0 = 0;
+                if (DEV) {
+#pragma unroll
+                    for (int j = 1; j < QU; ++j) d0 -= to_real(fc[(long long)(j - 1) * n + s]);
+                }
+#pragma unroll
+                for (int j = 0; j < QU; ++j) {
+                    const int ex = UL::ex(j), ey = UL::ey(j), ez = UL::ez(j);
+                    const R hs = s_h[sh(zp - ez) * RP + (py - ey) * RX + (px - ex)];
+                    const long long src = s + off(-ex, -ey, -ez);
+                    R fj;
+                    if (!DEV) {
+                        fj = om_u * to_real(fc[(long long)j * n + src]) + R(UL::w(j)) * hs;
+                    } else {
+                        const R dj = (j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]);
+                        fj = R(UL::w(j)) * hs + om_u * dj;
+                    }
+                    fv[j] = fj;
+                    u += fj;
+                }
+                if (inner) {
+                    if (!DEV) {
+#pragma unroll
+                        for (int j = 0; j < QU; ++j) fn[(long long)j * n + s] = from_real<T, R>(fv[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 1; j < QU; ++j)
+                            fn[(long long)(j - 1) * n + s] = from_real<T, R>(fv[j] - R(UL::w(j)) * u);
+                    }
+                }
+            } else {
+                if (!DEV) {
+#pragma unroll
+                    for (int j = 0; j < QU; ++j) u += to_real(fc[(long long)j * n + s]);
+                } else {
+                    u = s_h[sh(zp) * RP + py * RX + px];  // C^n + phi^n / 2
+                }
+            }
+            if (inner) auxn[s] = DEV ? (u - R(0.5) * ph) : (u * ieu - R(0.5) * ph);
+
+            // gradient of phi^n (Sec. 4.2)
+            R Gx = 0, Gy = 0, Gz = 0;
+            if (args.grad == LBPF_GRAD_DD) {
+                // Eq. (Def_DeriveeDirectionnelle) and Eq. (Grad_DF-Centree)
+#pragma unroll
+                for (int i = 1; i < QG; ++i) {
+                    const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
+                    const R dd = s_phi[sphi(zp + ez) * RP + (py + ey) * RX + (px + ex)] -
+                                 s_phi[sphi(zp - ez) * RP + (py - ey) * RX + (px - ex)];
+                    const R wd = R(PL::w(i)) * dd;
+                    if (ex) Gx += R(ex) * wd;
+                    if (ey) Gy += R(ey) * wd;
+                    if (ez) Gz += R(ez) * wd;
+                }
+                const R k = R(0.5 / PL::E2);
+                Gx *= k;
+                Gy *= k;
+                Gz *= k;
+            } else {
+                const R* pl = s_phi + sphi(zp) * RP;
+                Gx = R(0.5) * (pl[py * RX + px + 1] - pl[py * RX + px - 1]);
+                Gy = R(0.5) * (pl[(py + 1) * RX + px] - pl[(py - 1) * RX + px]);
+                if (D == 3)
+                    Gz = R(0.5) * (s_phi[sphi(zp + 1) * RP + py * RX + px] - s_phi[sphi(zp - 1) * RP + py * RX + px]);
+            }
+
+            // crystal index (Sec. 4.3): keep a non-zero index; otherwise take
+            // the first non-zero neighbour (axes before diagonals) where
+            // |grad phi| > xi.
+            int cryst = 1;
+            if (use_index) {
+                int Iv = s_I[sphi(zp) * RP + py * RX + px];
+                if (Iv == 0 && Gx * Gx + Gy * Gy + Gz * Gz > xi2) {
+#pragma unroll
+                    for (int i = 1; i < QG; ++i) {
+                        const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
+                        const int v = s_I[sphi(zp + ez) * RP + (py + ey) * RX + (px + ex)];
+                        if (Iv == 0 && v != 0) Iv = v;
+                    }
+                }
+                if (inner) In[s] = (int8_t)Iv;
+                cryst = Iv;
+            }
+
+            R a = 1, Nx = 0, Ny = 0, Nz = 0;
+            if (cryst > 0 && cryst <= dm.n_crystals) anisotropy<R, D>(dm.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
+
+            const R A2 = a * a;
+            const R iA2 = R(1) / A2;
+            const R ieta = R(1) / (A2 * De2 + R(0.5));
+            const R omp = (R(1) - ph) * (R(1) + ph);
+            const R Qphi = (ph - lam * u * omp) * omp;
+            const R vf = -De2 * ieta * iA2;
+            const int ci = ly * CX + lx;
+            dco[0 * CP + ci] = (R(1) - ieta) * iA2;
+            dco[1 * CP + ci] = iA2 - R(1);
+            dco[2 * CP + ci] = (ph * ieta + qphi * Qphi) * iA2;
+            dco[3 * CP + ci] = vf * Nx;
+            dco[4 * CP + ci] = vf * Ny;
+            if (D == 3) dco[5 * CP + ci] = vf * Nz;
+        }
+    };
+
+    // -- phase-field collision + streaming for the tile interior of plane z ----
+    auto output_plane = [&](int z) {
+        const int ltx = tid % TX, lty = tid / TX;
+        if (ltx >= tw || lty >= th) return;
+        const int gx = x0 + ltx, gy = y0 + lty;
+        const long long s = (long long)z * nxy + (long long)gy * nx + gx;
+        const int gxm = wrapx(gx - 1), gxp = wrapx(gx + 1);
+        const int gym = wrapy(gy - 1), gyp = wrapy(gy + 1);
+        const long long oxm = gxm - gx, oxp = gxp - gx;
+        const long long oym = (long long)(gym - gy) * nx, oyp = (long long)(gyp - gy) * nx;
+        long long ozm = 0, ozp = 0;
+        if (D == 3) {
+            ozm = (long long)(wrapz(z - 1) - z) * nxy;
+            ozp = (long long)(wrapz(z + 1) - z) * nxy;
+        }
+        auto off = [&](int ex, int ey, int ez) -> long long {
+            return (ex < 0 ? oxm : (ex > 0 ? oxp : 0)) + (ey < 0 ? oym : (ey > 0 ? oyp : 0)) +
+                   (D == 3 ? (ez < 0 ? ozm : (ez > 0 ? ozp : 0)) : 0);
+        };
+        const int px = ltx + 2, py = lty + 2;  // halo-2 frame
+        const int cx = ltx + 1, cy = lty + 1;  // halo-1 frame
+        R gl[QG];
+        if (!DEV) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gl[i] = to_real(gc[(long long)i * n + s]);
+        } else {
+            const R phy = s_phi[sphi(z) * RP + py * RX + px];
+            R d0 = 0;
+#pragma unroll
+            for (int i = 1; i < QG; ++i) {
+                const R d = to_real(gc[(long long)(i - 1) * n + s]);
+                d0 -= d;
+                gl[i] = R(PL::w(i)) * phy + d;
+            }
+            gl[0] = R(PL::w(0)) * phy + d0;
+        }
+        R gnew[QG];
+        R phinew = 0;
+#pragma unroll
+        for (int i = 0; i < QG; ++i) {
+            const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
+            const R* co = s_co + sco(z - ez) * NCO * CP + (cy - ey) * CX + (cx - ex);
+            R gp;
+            if (i == 0) {
+                gp = gl[0];
+            } else if (!DEV) {
+                gp = to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
+            } else {
+                const R phs = s_phi[sphi(z - ez) * RP + (py - ey) * RX + (px - ex)];
+                gp = R(PL::w(i)) * phs + to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
+            }
+            R ev = R(0);
+            if (ex) ev += R(ex) * co[3 * CP];
+            if (ey) ev += R(ey) * co[4 * CP];
+            if (D == 3 && ez) ev += R(ez) * co[5 * CP];
+            const R v = co[0] * gp - co[CP] * gl[i] + R(PL::w(i)) * (co[2 * CP] + ev);
+            gnew[i] = v;
+            phinew += v;
+        }
+        phin[s] = phinew;
+        if (!DEV) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gn[(long long)i * n + s] = from_real<T, R>(gnew[i]);
+        } else {
+#pragma unroll
+            for (int i = 1; i < QG; ++i)
+                gn[(long long)(i - 1) * n + s] = from_real<T, R>(gnew[i] - R(PL::w(i)) * phinew);
+        }
+    };
+
+    if constexpr (D == 2) {
+        load_plane(0);
+        __syncthreads();
+        coef_plane(0, true);
+        __syncthreads();
+        output_plane(0);
+    } else {
+        const int z0 = it.z0, z1 = it.z1;
+        load_plane(z0 - 2);
+        load_plane(z0 - 1);
+        load_plane(z0);
+        __syncthreads();
+        coef_plane(z0 - 1, false);
+        __syncthreads();
+        load_plane(z0 + 1);
+        __syncthreads();
+        coef_plane(z0, true);
+        for (int z = z0; z < z1; ++z) {
+            __syncthreads();
+            load_plane(z + 2);
+            __syncthreads();
+            coef_plane(z + 1, z + 1 < z1);
+            __syncthreads();
+            output_plane(z);
+        }
+    }
+}
+
+template <class PL, class UL, class S>
+constexpr size_t step_smem_bytes()
+{
+    using R = typename S::Real;
+    constexpr int D = PL::D;
+    constexpr int RP = (TX + 4) * (TY + 4), CP = (TX + 2) * (TY + 2);
+    constexpr int NPH = D == 3 ? 4 : 1, NH = D == 3 ? 3 : 1, NC = D == 3 ? 3 : 1, NCO = D + 3;
+    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (size_t)NPH * RP;
+}
+
+}  // namespace lbpf

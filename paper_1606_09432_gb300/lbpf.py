@@ -1,0 +1,248 @@
+"""Thin Python binding of the lbpf C ABI (include/lbpf.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+liblbpf.so.  Device buffers may be passed as torch CUDA tensors, host buffers
+as numpy arrays.  There is no CPU fallback: if the library is missing, loading
+fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbpf.so")
+
+# enums (include/lbpf.h)
+LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_ETIMEOUT, LBPF_ENONFINITE, LBPF_ERANGE = 0, -1, -2, -3, -4, -5, -6
+LBPF_D2Q9_D2Q5, LBPF_D3Q15_D3Q7, LBPF_D3Q19_D3Q7, LBPF_D3Q27_D3Q7 = 0, 1, 2, 3
+LBPF_GRAD_DD, LBPF_GRAD_FD = 0, 1
+LBPF_FP64, LBPF_FP32, LBPF_FP32_FP16DEV, LBPF_FP32_BF16DEV = 0, 1, 2, 3
+LBPF_AS_CUBIC100, LBPF_AS_ANGLE, LBPF_AS_Y66, LBPF_AS_HOYT110, LBPF_AS_S111 = 0, 1, 2, 3, 4
+LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
+LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS = range(6)
+LBPF_MAX_CRYSTALS = 16
+EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
+            "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error"]
+
+
+class lbpf_crystal(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("gamma", C.c_double), ("q", C.c_int), ("phi0", C.c_double)]
+
+
+class lbpf_domain(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dt", C.c_double), ("W0", C.c_double), ("tau0", C.c_double),
+                ("kappa", C.c_double), ("lam", C.c_double), ("delta", C.c_double), ("xi", C.c_double),
+                ("n_crystals", C.c_int), ("crystals", lbpf_crystal * LBPF_MAX_CRYSTALS)]
+
+
+class lbpf_seed_t(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("radius", C.c_double), ("crystal", C.c_int)]
+
+
+class LbpfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbpf error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbpf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1606_09432_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.lbpf_create.argtypes = [C.POINTER(lbpf_domain), C.c_int, C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp)]
+    lib.lbpf_seed.argtypes = [vp, C.c_int, C.POINTER(lbpf_seed_t), C.c_int]
+    lib.lbpf_write_fields.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+    lib.lbpf_step.argtypes = [vp, C.c_int]
+    lib.lbpf_read_field.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_size_t]
+    lib.lbpf_read_populations.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_size_t]
+    d = C.POINTER(C.c_double)
+    lib.lbpf_measure.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, d, d, d]
+    lib.lbpf_query.argtypes = [vp, C.c_int, d]
+    lib.lbpf_destroy.argtypes = [vp]
+    lib.lbpf_last_error.argtypes = [vp]
+    lib.lbpf_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        lib[name].restype = lib[name].restype if name == "lbpf_last_error" else C.c_int
+    _lib = lib
+    return lib
+
+
+def lbpf_last_error(ctx=None) -> str:
+    return load().lbpf_last_error(ctx).decode()
+
+
+def _check(rc, ctx=None):
+    if rc != LBPF_OK:
+        raise LbpfError(rc, lbpf_last_error(ctx))
+
+
+def make_crystal(kind=LBPF_AS_CUBIC100, eps=0.0, gamma=0.0, q=4, phi0=0.0) -> lbpf_crystal:
+    return lbpf_crystal(kind, eps, gamma, q, phi0)
+
+
+def make_domain(nx, ny, nz=1, *, dx, dt, W0, tau0, kappa, lam=0.0, delta=0.0, xi=1e-7, crystals=None) -> lbpf_domain:
+    """lam <= 0 selects lambda* (the library applies Eq. (Kinetic-Coeff) with beta = 0)."""
+    d = lbpf_domain()
+    d.nx, d.ny, d.nz = nx, ny, nz
+    d.dx, d.dt, d.W0, d.tau0, d.kappa = dx, dt, W0, tau0, kappa
+    d.lam = 0.0 if lam is None else lam
+    d.delta, d.xi = delta, xi
+    cl = list(crystals) if crystals else [make_crystal()]
+    d.n_crystals = len(cl)
+    for k, c in enumerate(cl):
+        d.crystals[k] = c
+    return d
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+def lbpf_create(domains, lattice, grad=LBPF_GRAD_DD, precision=LBPF_FP32, stream=None):
+    doms = list(domains) if isinstance(domains, (list, tuple)) else [domains]
+    arr = (lbpf_domain * len(doms))(*doms)
+    ctx = C.c_void_p()
+    s = C.c_void_p(stream) if stream else None
+    _check(load().lbpf_create(arr, len(doms), lattice, grad, precision, s, C.byref(ctx)))
+    return ctx
+
+
+def lbpf_seed(ctx, domain, seeds):
+    rows = [lbpf_seed_t(*(float(v) for v in s[:4]), int(s[4]) if len(s) > 4 else 0) for s in seeds]
+    arr = (lbpf_seed_t * len(rows))(*rows)
+    _check(load().lbpf_seed(ctx, domain, arr, len(rows)), ctx)
+
+
+def lbpf_write_fields(ctx, domain, phi, u, index=None):
+    pp, dev = _ptr(phi)
+    up, dev2 = _ptr(u)
+    ip = None
+    if index is not None:
+        ip, dev3 = _ptr(index)
+        if dev3 != dev:
+            raise ValueError("index must live where phi does")
+    if dev != dev2:
+        raise ValueError("phi and u must both be host or both device buffers")
+    _check(load().lbpf_write_fields(ctx, domain, pp, up, ip, dev), ctx)
+
+
+def lbpf_step(ctx, n_steps=1):
+    _check(load().lbpf_step(ctx, int(n_steps)), ctx)
+
+
+def lbpf_read_field(ctx, domain, field, out):
+    p, dev = _ptr(out)
+    nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+    _check(load().lbpf_read_field(ctx, domain, field, p, dev, nbytes), ctx)
+    return out
+
+
+def lbpf_read_populations(ctx, domain, which, out):
+    p, dev = _ptr(out)
+    nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+    _check(load().lbpf_read_populations(ctx, domain, which, p, dev, nbytes), ctx)
+    return out
+
+
+def lbpf_measure(ctx, domain, cx, cy, cz=0):
+    tip = (C.c_double * 6)()
+    sf, cs = C.c_double(), C.c_double()
+    _check(load().lbpf_measure(ctx, domain, cx, cy, cz, tip, C.byref(sf), C.byref(cs)), ctx)
+    return np.array(tip[:]), sf.value, cs.value
+
+
+def lbpf_query(ctx, what):
+    v = C.c_double()
+    _check(load().lbpf_query(ctx, what, C.byref(v)), ctx)
+    return v.value
+
+
+def lbpf_destroy(ctx):
+    if ctx:
+        load().lbpf_destroy(ctx)
+
+
+class Solver:
+    """Convenience owner of one context (all domains share lattice, gradient
+    and precision)."""
+
+    Q = {LBPF_D2Q9_D2Q5: (9, 5), LBPF_D3Q15_D3Q7: (15, 7), LBPF_D3Q19_D3Q7: (19, 7), LBPF_D3Q27_D3Q7: (27, 7)}
+
+    def __init__(self, domains, lattice, grad=LBPF_GRAD_DD, precision=LBPF_FP32, stream=None):
+        self.domains = list(domains) if isinstance(domains, (list, tuple)) else [domains]
+        self.precision = precision
+        self.lattice = lattice
+        self.ctx = lbpf_create(self.domains, lattice, grad, precision, stream)
+
+    @property
+    def dtype(self):
+        return np.float64 if self.precision == LBPF_FP64 else np.float32
+
+    def shape(self, domain=0):
+        d = self.domains[domain]
+        return (d.nz, d.ny, d.nx)
+
+    def seed(self, seeds, domain=0):
+        lbpf_seed(self.ctx, domain, seeds)
+        return self
+
+    def write_fields(self, phi, u, index=None, domain=0):
+        if not hasattr(phi, "data_ptr"):
+            phi = np.ascontiguousarray(phi, dtype=self.dtype)
+            u = np.ascontiguousarray(u, dtype=self.dtype)
+            if index is not None:
+                index = np.ascontiguousarray(index, dtype=np.int32)
+        lbpf_write_fields(self.ctx, domain, phi, u, index)
+        return self
+
+    def step(self, n=1):
+        lbpf_step(self.ctx, n)
+        return self
+
+    def field(self, which, domain=0):
+        dt = np.int32 if which == LBPF_FIELD_INDEX else self.dtype
+        out = np.empty(self.shape(domain), dtype=dt)
+        return lbpf_read_field(self.ctx, domain, which, out)
+
+    def fields(self, domain=0):
+        return self.field(LBPF_FIELD_PHI, domain), self.field(LBPF_FIELD_U, domain)
+
+    def populations(self, which, domain=0):
+        out = np.empty((self.Q[self.lattice][which],) + self.shape(domain), dtype=self.dtype)
+        return lbpf_read_populations(self.ctx, domain, which, out)
+
+    def measure(self, cx, cy, cz=0, domain=0):
+        return lbpf_measure(self.ctx, domain, cx, cy, cz)
+
+    def query(self, what):
+        return lbpf_query(self.ctx, what)
+
+    def close(self):
+        if self.ctx:
+            lbpf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Bars: FP64 GPU vs oracle <= 1e-10 max-abs on phi and u (2000 steps on the
+128^2 2D configuration, both gradient operators); FP32 <= 1e-4 with tips
+within 0.5 lattice unit; 16-bit deviation storage: errors reported with loose
+sanity bounds (the deviation form changes the method's rounding, not its
+arithmetic).
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_run, maxabs, oracle_run
+from paper_1606_09432_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1606_09432_gb300 import build as B
+    from paper_1606_09432_gb300 import lbpf
+    B.build()
+    lbpf.load()
+    return lbpf
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+C2P = dict(W.C3D_PARAMS, delta=0.3)
+
+
+@pytest.mark.parametrize("grad", [0, 1])
+def test_c1_fp64_2000_steps(L, O, grad):
+    w = W.c1(128)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 0, w["shape"], w["params"], cr, seeds=w["seeds"], grad=grad)
+    s = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"], grad=grad)
+    phi0, u0 = s.fields()
+    assert maxabs(phi0, o.fields()[0]) < 1e-14 and maxabs(u0, o.fields()[1]) == 0.0
+    o.step(2000)
+    s.step(2000)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    assert maxabs(phi, ophi) <= 1e-10
+    assert maxabs(u, ou) <= 1e-10
+    assert maxabs(phi, phi0) > 0.1  # the crystal grew
+    tip, sf, cs = s.measure(*w["centre"])
+    otip, osf, ocs = o.measure(*w["centre"])
+    assert np.abs(tip - otip).max() < 1e-9 and abs(sf - osf) < 1e-12 and abs(cs - ocs) < 1e-9 * abs(ocs)
+
+
+FORMS3 = {"cubic": dict(kind=0, eps=0.05), "hoyt": dict(kind=3, eps=0.0, gamma=-0.02),
+          "s111": dict(kind=4, gamma=0.02), "y66": dict(kind=2, eps=0.05), "hoyt_mix": dict(kind=3, eps=0.02, gamma=0.02)}
+
+
+@pytest.mark.parametrize("lattice", [1, 2, 3])
+@pytest.mark.parametrize("form", list(FORMS3))
+def test_fp64_3d_ragged(L, O, lattice, form):
+    shape = (18, 21, 37)  # several tiles along x and y, ragged everywhere
+    seeds = [(18.5, 10.2, 8.7, 5.0, 0)]
+    cr = [FORMS3[form]]
+    o = oracle_run(O, lattice, shape, C2P, cr, seeds=seeds)
+    s = gpu_run(L, lattice, shape, C2P, cr, seeds=seeds)
+    o.step(60)
+    s.step(60)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    assert maxabs(phi, ophi) <= 1e-10 and maxabs(u, ou) <= 1e-10
+
+
+@pytest.mark.parametrize("form", [dict(kind=1, eps=0.05, q=5, phi0=0.3), dict(kind=2, eps=0.05),
+                                  dict(kind=3, eps=0.02, gamma=-0.02), dict(kind=0, eps=0.04)])
+@pytest.mark.parametrize("grad", [0, 1])
+def test_fp64_2d_forms(L, O, form, grad):
+    shape = (1, 37, 45)
+    seeds = [(20.3, 17.6, 0, 6.0, 0)]
+    o = oracle_run(O, 0, shape, W.C1_PARAMS, [form], seeds=seeds, grad=grad)
+    s = gpu_run(L, 0, shape, W.C1_PARAMS, [form], seeds=seeds, grad=grad)
+    o.step(300)
+    s.step(300)
+    phi, u = s.fields()
+    assert maxabs(phi, o.fields()[0]) <= 1e-10 and maxabs(u, o.fields()[1]) <= 1e-10
+
+
+def test_fp64_multicrystal_index(L, O):
+    shape = (1, 50, 70)
+    prm = dict(W.C4_PARAMS, delta=0.35)
+    crs = [dict(kind=1, eps=0.04, q=4, phi0=0.785), dict(kind=1, eps=0.04, q=5, phi0=0.087),
+           dict(kind=1, eps=0.04, q=6, phi0=0.0)]
+    seeds = [(15.0, 14.0, 0, 5.0, 0), (50.0, 18.0, 0, 6.0, 1), (35.0, 38.0, 0, 4.5, 2)]
+    o = oracle_run(O, 0, shape, prm, crs, seeds=seeds, xi=1e-1)
+    s = gpu_run(L, 0, shape, prm, crs, seeds=seeds, xi=1e-1)
+    I0 = s.field(L.LBPF_FIELD_INDEX)
+    assert np.array_equal(I0, o.fields()[2])
+    for _ in range(4):
+        o.step(75)
+        s.step(75)
+        phi, u = s.fields()
+        ophi, ou, oI = o.fields()
+        assert maxabs(phi, ophi) <= 1e-10 and maxabs(u, ou) <= 1e-10
+        assert np.array_equal(s.field(L.LBPF_FIELD_INDEX), oI)
+    assert (oI == 0).any() and set(np.unique(oI)) == {0, 1, 2, 3}
+    assert (oI != I0).any()  # the index field spread
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_populations_match(L, O, lattice):
+    shape = (1, 33, 40) if lattice == 0 else (10, 12, 35)
+    prm = W.C1_PARAMS if lattice == 0 else C2P
+    seeds = [(17.0, 15.0, 5.0, 5.0, 0)]
+    cr = [dict(kind=0, eps=0.05)]
+    o = oracle_run(O, lattice, shape, prm, cr, seeds=seeds)
+    s = gpu_run(L, lattice, shape, prm, cr, seeds=seeds)
+    o.step(11)
+    s.step(11)
+    og, of = o.populations()
+    assert maxabs(s.populations(0), og) <= 1e-12
+    assert maxabs(s.populations(1), of) <= 1e-12
+
+
+def test_write_fields_3d(L, O):
+    shape = (12, 14, 40)
+    rng = np.random.default_rng(5)
+    z, y, x = np.mgrid[0:12, 0:14, 0:40]
+    phi = np.tanh(2.0 * np.sin(2 * np.pi * x / 40) * np.cos(2 * np.pi * y / 14) + 0.3 * np.sin(2 * np.pi * z / 12))
+    u = -0.3 + 0.05 * rng.standard_normal(shape)
+    cr = [dict(kind=3, eps=0.02, gamma=-0.02)]
+    o = oracle_run(O, 1, shape, C2P, cr, fields=(phi, u))
+    s = gpu_run(L, 1, shape, C2P, cr, fields=(phi, u))
+    o.step(30)
+    s.step(30)
+    p, uu = s.fields()
+    assert maxabs(p, o.fields()[0]) <= 1e-10 and maxabs(uu, o.fields()[1]) <= 1e-10
+
+
+def test_split_steps(L):
+    w = W.c1(64)
+    cr = [w["aniso"]]
+    a = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"])
+    b = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"])
+    a.step(12)
+    b.step(7)
+    b.fields()  # forces the heat catch-up in the middle
+    b.step(5)
+    assert maxabs(a.fields()[0], b.fields()[0]) <= 1e-13 and maxabs(a.fields()[1], b.fields()[1]) <= 1e-13
+    b.step(0)
+    assert a.query(L.LBPF_Q_STEPS) == 12 and b.query(L.LBPF_Q_STEPS) == 12
+
+
+def test_multi_domain_context(L):
+    sizes = [(1, 40, 70), (1, 33, 33), (1, 64, 50)]
+    prm = dict(W.C4_PARAMS, delta=0.3)
+    cr = [dict(kind=1, eps=0.05, q=4, phi0=0.2)]
+    doms = [L.make_domain(n[2], n[1], 1, lam=10.0, crystals=[L.make_crystal(**cr[0])],
+                          **{k: v for k, v in prm.items() if k != "lam"}) for n in sizes]
+    multi = L.Solver(doms, 0, 0, L.LBPF_FP64)
+    singles = []
+    for k, n in enumerate(sizes):
+        seeds = [(n[2] / 2, n[1] / 2, 0, 5.0 + k, 0)]
+        multi.seed(seeds, domain=k)
+        singles.append(gpu_run(L, 0, n, prm, cr, seeds=seeds))
+    multi.step(150)
+    for k, s in enumerate(singles):
+        s.step(150)
+        assert np.array_equal(multi.field(0, domain=k), s.field(0))
+        assert np.array_equal(multi.field(1, domain=k), s.field(1))
+
+
+def test_tiny_domains(L, O):
+    for lattice, shape in ((0, (1, 2, 2)), (0, (1, 3, 2)), (1, (2, 2, 2)), (3, (3, 2, 5))):
+        prm = W.C1_PARAMS if lattice == 0 else C2P
+        rng = np.random.default_rng(1)
+        phi = np.tanh(rng.standard_normal(shape))
+        u = -0.2 + 0.01 * rng.standard_normal(shape)
+        cr = [dict(kind=0, eps=0.05)]
+        o = oracle_run(O, lattice, shape, prm, cr, fields=(phi, u))
+        s = gpu_run(L, lattice, shape, prm, cr, fields=(phi, u))
+        o.step(20)
+        s.step(20)
+        assert maxabs(s.fields()[0], o.fields()[0]) <= 1e-12, shape
+
+
+def test_errors(L):
+    d = L.make_domain(1, 8, 1, dx=1, dt=0.1, W0=1, tau0=1, kappa=1)
+    with pytest.raises(L.LbpfError) as e:
+        L.Solver(d, 0)
+    assert e.value.code == L.LBPF_EINVAL
+    d = L.make_domain(16, 16, 1, dx=1, dt=0.1, W0=1, tau0=1, kappa=1,
+                      crystals=[L.make_crystal(L.LBPF_AS_ANGLE, eps=0.05, q=4)])
+    with pytest.raises(L.LbpfError):
+        L.Solver(d, 1)  # 2D domain on a 3D lattice
+    s = L.Solver(d, 0, precision=L.LBPF_FP64).seed([(8, 8, 0, 3, 0)])
+    with pytest.raises(L.LbpfError) as e:
+        L.lbpf_read_field(s.ctx, 0, 0, np.zeros(10))
+    assert e.value.code == L.LBPF_ERANGE
+    with pytest.raises(L.LbpfError):
+        s.seed([(8, 8, 0, 3, 5)])  # crystal out of range
+    with pytest.raises(L.LbpfError):
+        L.lbpf_step(s.ctx, -1)
+    phi = np.zeros((1, 16, 16))
+    phi[0, 3, 3] = np.nan
+    s.write_fields(phi, np.zeros((1, 16, 16)))
+    with pytest.raises(L.LbpfError) as e:
+        s.measure(8, 8)
+    assert e.value.code == L.LBPF_ENONFINITE
+
+
+def test_fp32_3d_vs_oracle(L, O):
+    w = W.c2(48)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 1, w["shape"], w["params"], cr, seeds=w["seeds"], precision=L.LBPF_FP32)
+    for _ in range(4):
+        o.step(250)
+        s.step(250)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    e_phi, e_u = maxabs(phi, ophi), maxabs(u, ou)
+    tip = s.measure(*w["centre"])[0]
+    otip = o.measure(*w["centre"])[0]
+    print(f"FP32 vs FP64 oracle after 1000 steps: phi {e_phi:.2e}, u {e_u:.2e}, tips {np.abs(tip - otip).max():.2e}")
+    assert e_phi <= 1e-4 and e_u <= 1e-4
+    assert np.abs(tip - otip).max() <= 0.5
+    assert otip[0] > 9.0  # grew
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_dev16_vs_oracle(L, O, precision):
+    w = W.c3(48, eps=0.0, gamma=-0.02)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 1, w["shape"], w["params"], cr, seeds=w["seeds"], precision=precision)
+    _, _, c0 = s.measure(*w["centre"])
+    o.step(500)
+    s.step(500)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    e_phi, e_u = maxabs(phi, ophi), maxabs(u, ou)
+    tip = s.measure(*w["centre"])[0]
+    otip = o.measure(*w["centre"])[0]
+    _, _, c1 = s.measure(*w["centre"])
+    print(f"16-bit deviations ({'FP16' if precision == 2 else 'BF16'}) vs FP64 oracle after 500 steps: "
+          f"phi {e_phi:.2e}, u {e_u:.2e}, tips {np.abs(tip - otip).max():.2e}, "
+          f"conservation drift {abs(c1 - c0) / abs(c0):.2e}")
+    assert np.isfinite(phi).all() and np.isfinite(u).all()
+    assert e_phi < 5e-2 and e_u < 5e-2 and np.abs(tip - otip).max() < 1.0
+
+
+def test_fp64_conservation_gpu(L):
+    w = W.c1(128)
+    s = gpu_run(L, 0, w["shape"], w["params"], [w["aniso"]], seeds=w["seeds"])
+    _, _, c0 = s.measure(*w["centre"])
+    s.step(2000)
+    _, _, c1 = s.measure(*w["centre"])
+    assert abs(c1 - c0) <= 1e-12 * abs(c0)
+
+
+def test_full_size_first_steps(L, O):
+    """256^3 D3Q15/D3Q7 FP32, the benchmark's configuration and launch: two
+    steps against the FP64 oracle on the whole field."""
+    w = W.c2(256)
+    cr = [w["aniso"]]
+    s = gpu_run(L, 1, w["shape"], w["params"], cr, seeds=w["seeds"], precision=L.LBPF_FP32)
+    o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s.step(2)
+    o.step(2)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    assert maxabs(phi, ophi) <= 1e-5 and maxabs(u, ou) <= 1e-5
+
+
+def test_full_size_invariants(L):
+    """256^3 FP32 after 400 steps: cubic symmetry of the centred crystal and
+    conservation of sum(u - phi/2) (FP64 sums on the GPU)."""
+    w = W.c2(256)
+    s = gpu_run(L, 1, w["shape"], w["params"], [w["aniso"]], seeds=w["seeds"], precision=L.LBPF_FP32)
+    tip0, _, c0 = s.measure(*w["centre"])
+    s.step(400)
+    tip, sf, c1 = s.measure(*w["centre"])
+    assert abs(c1 - c0) <= 1e-5 * abs(c0)
+    assert tip[0] > tip0[0] + 0.5
+    assert np.abs(tip - tip[0]).max() < 1e-3  # six equal arms
+    phi = s.field(0)
+    c = 128
+    core = phi[c - 40:c + 41, c - 40:c + 41, c - 40:c + 41]
+    assert maxabs(core, core[::-1]) < 1e-4
+    assert maxabs(core, core.transpose(1, 0, 2)) < 1e-4
+    assert maxabs(core, core.transpose(2, 1, 0)) < 1e-4
