@@ -133,8 +133,9 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_solver(L, W, workload, stream):
+def make_solver(L, W, workload, stream, size=0):
     desc, lattice, precision, n = WORKLOADS[workload]
+    n = size or n
     w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
     prm = dict(w["params"])
     lam = prm.pop("lam")
@@ -206,6 +207,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2-256-fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--size", type=int, default=0, help="override the cube edge of the workload (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -234,8 +236,10 @@ def main():
 
     stream = torch.cuda.Stream()
     desc, lattice, precision, n = WORKLOADS[args.workload]
+    if args.size:
+        desc = desc.replace(f"{n}^3", f"{args.size}^3")
     with torch.cuda.stream(stream):
-        s, w = make_solver(L, W, args.workload, stream.cuda_stream)
+        s, w = make_solver(L, W, args.workload, stream.cuda_stream, args.size)
     sites = s.query(L.LBPF_Q_SITES)
     bps = s.query(L.LBPF_Q_BYTES_PER_SITE)
 

@@ -369,12 +369,13 @@ static int as_value(const orc_crystal* c, int D, const double n[3], double* a, d
  * with n = -grad(phi) / |grad(phi)|, Eq. (Def_Normal_Vector).  The chain rule
  * through n gives d n_b / d(d_a phi) = -(delta_ab - n_a n_b) / |grad phi|.
  * Reading (zero-gradient guard, the paper is silent): where
- * |grad phi|^2 dx^2 <= 1e-30 the normal is undefined; there a_s = 1, N = 0. */
+ * |grad phi| dx <= 1e-10 the normal is undefined (or set by rounding noise,
+ * e.g. at symmetry centres of an unsaturated field); there a_s = 1, N = 0. */
 int orc_anisotropy(const orc_crystal* c, int D, double dx, const double G[3], double* a, double N[3])
 {
     double g2 = G[0] * G[0] + G[1] * G[1] + (D == 3 ? G[2] * G[2] : 0.0);
     N[0] = N[1] = N[2] = 0.0;
-    if (g2 * dx * dx <= 1e-30) {
+    if (g2 * dx * dx <= 1e-20) {
         *a = 1.0;
         return 0;
     }

@@ -195,14 +195,20 @@ template <class R> __device__ __forceinline__ R rsqrt_r(R x);
 template <> __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_r<double>(double x) { return 1.0 / sqrt(x); }
 
+// Zero-gradient guard: below |G| = 1e-10 (FP64) or 1e-6 (FP32) lattice units
+// the direction of G is undefined or set by rounding noise (e.g. at symmetry
+// centres); there a_s = 1 and N = 0.
+template <class R> __device__ __forceinline__ R guard2();
+template <> __device__ __forceinline__ double guard2<double>() { return 1e-20; }
+template <> __device__ __forceinline__ float guard2<float>() { return 1e-12f; }
+
 template <class R, int D>
 __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz, R& a, R& Nx, R& Ny, R& Nz)
 {
     const R g2 = Gx * Gx + Gy * Gy + (D == 3 ? Gz * Gz : R(0));
     Nx = Ny = Nz = R(0);
     a = R(1);
-    // Zero-gradient guard (the normal is undefined): a_s = 1, N = 0.
-    if (!(g2 > R(1e-30))) return;
+    if (!(g2 > guard2<R>())) return;
     const R eps = R(c.eps), gam = R(c.gamma);
     if (c.kind == LBPF_AS_ANGLE) {
         // Eq. (As_Theta), varphi = atan2(n_y, n_x) with n = -G/|G|;
