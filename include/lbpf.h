@@ -217,6 +217,28 @@ typedef enum {
 /* Read a property of the context into *value. */
 int lbpf_query(const lbpf_ctx* ctx, int what, double* value);
 
+/* The two measurement sums of lbpf_measure (sum of (1 + phi)/2 and sum of
+ * u - phi/2, FP64 accumulation) over caller-provided fields, for callers that
+ * cannot allocate device memory when they call: applications that hand all
+ * device memory to their own pool allocator (an allocation by this library
+ * would fail or fragment the pool) and latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   phi, u: device arrays of n elements (double for LBPF_FP64, float for the
+ *           other precisions), e.g. filled by lbpf_read_field(out_on_device=1).
+ *   n:      1 .. 268435456 sites; larger sizes return LBPF_ERANGE.
+ *   out:    device array of 3 doubles: sum (1 + phi)/2, sum (u - phi/2), and
+ *           the number of non-finite phi or u values.
+ *   stream: cudaStream_t or NULL; the call is asynchronous on it.
+ * Allocates nothing: its scratch is a fixed 96 KiB device array that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * each device looks up that array's device address (set-up work); make it
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors: LBPF_EINVAL (NULL pointer, bad precision), LBPF_ERANGE, LBPF_ECUDA. */
+int lbpf_field_sums_static(const void* phi, const void* u, long long n, int precision, double* out,
+                           void* stream);
+
 /* Release every resource of the context (NULL is accepted).  Synchronises
  * the stream first. */
 int lbpf_destroy(lbpf_ctx* ctx);

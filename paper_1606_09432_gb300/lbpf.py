@@ -25,7 +25,8 @@ LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
 LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS = range(6)
 LBPF_MAX_CRYSTALS = 16
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
-            "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error"]
+            "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
+            "lbpf_field_sums_static"]
 
 
 class lbpf_crystal(C.Structure):
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH):
     lib.lbpf_destroy.argtypes = [vp]
     lib.lbpf_last_error.argtypes = [vp]
     lib.lbpf_last_error.restype = C.c_char_p
+    lib.lbpf_field_sums_static.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp]
     for name in EXPORTED:
         lib[name].restype = lib[name].restype if name == "lbpf_last_error" else C.c_int
     _lib = lib
@@ -174,6 +176,20 @@ def lbpf_query(ctx, what):
     v = C.c_double()
     _check(load().lbpf_query(ctx, what, C.byref(v)), ctx)
     return v.value
+
+
+def lbpf_field_sums_static(phi, u, precision, out, stream=None):
+    """Measurement sums over device tensors phi, u into the device tensor out
+    (3 float64), with no device allocation by the library; see include/lbpf.h."""
+    pp, d1 = _ptr(phi)
+    up, d2 = _ptr(u)
+    op, d3 = _ptr(out)
+    if not (d1 and d2 and d3):
+        raise ValueError("phi, u and out must be device tensors")
+    n = phi.numel()
+    rc = load().lbpf_field_sums_static(pp, up, n, precision, op, C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_field_sums_static failed")
 
 
 def lbpf_destroy(ctx):
