@@ -225,15 +225,24 @@ inline int grid_for(long long n)
 
 template <class PL, class UL, class S>
 struct LauncherImpl {
-    static cudaError_t step(const StepArgs& a, int n_items, size_t smem, cudaStream_t s)
+    static cudaError_t step(const StepArgs& a, int n_blocks, size_t smem, cudaStream_t s)
     {
-        step_kernel<PL, UL, S><<<n_items, NT, smem, s>>>(a);
+        step_kernel<PL, UL, S><<<n_blocks, NT, smem, s>>>(a);
         return cudaGetLastError();
     }
     static size_t smem() { return step_smem_bytes<PL, UL, S>(); }
     static cudaError_t prepare(size_t bytes)
     {
         return cudaFuncSetAttribute(step_kernel<PL, UL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+    static int blocks_per_sm(size_t bytes)
+    {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<PL, UL, S>, NT, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        return nb > 0 ? nb : 1;
     }
     static cudaError_t heat_sync(const DomainDev* d, int cur, int fcur, int acur, cudaStream_t s)
     {
@@ -259,7 +268,7 @@ struct LauncherImpl {
     }
     static const Launchers* get()
     {
-        static const Launchers L = {&step, &smem, &prepare, &heat_sync, &equilibrate, &read_u, &read_pops, PL::Q, UL::Q, PL::D};
+        static const Launchers L = {&step, &smem, &prepare, &blocks_per_sm, &heat_sync, &equilibrate, &read_u, &read_pops, PL::Q, UL::Q, PL::D};
         return &L;
     }
 };

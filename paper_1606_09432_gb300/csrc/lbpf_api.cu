@@ -16,6 +16,12 @@ namespace {
 
 thread_local std::string t_err;
 
+// Planes per z-segment of a work item of the step kernel.
+// (0: chosen from the work size and the resident block count.)
+#ifndef LBPF_SEGMENT
+#define LBPF_SEGMENT 0
+#endif
+
 // a2 of the thin-interface relations, Eq. (Kinetic-Coeff); lambda* cancels beta.
 constexpr double kA2 = 0.6267;
 
@@ -30,7 +36,8 @@ struct lbpf_ctx {
     std::vector<DomainDev> dd;
     DomainDev* d_dd = nullptr;
     WorkItem* d_items = nullptr;
-    int n_items = 0;
+    int* d_counters = nullptr;
+    int n_items = 0, n_blocks = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     const Launchers* L = nullptr;
@@ -98,21 +105,6 @@ static void free_all(lbpf_ctx* c)
 {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
-}
-
-// Planes per work item along z: enough items to fill the GPU several times
-// over, at least 8 planes each (each item recomputes two halo planes).
-static int choose_zchunk(long long tiles_xy, int nz)
-{
-    const char* env = getenv("LBPF_ZCHUNK");
-    if (env && atoi(env) > 0) return atoi(env) < nz ? atoi(env) : nz;
-    const long long target = 152LL * 4;
-    long long chunks = (target + tiles_xy - 1) / tiles_xy;
-    if (chunks < 1) chunks = 1;
-    long long zc = (nz + chunks - 1) / chunks;
-    if (zc < 8) zc = 8;
-    if (zc > nz) zc = nz;
-    return (int)zc;
 }
 
 extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattice, int grad, int precision,
@@ -219,25 +211,57 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
                 (h.use_index && cudaMemsetAsync(h.I[b], 0, (size_t)h.n, c->stream) != cudaSuccess))
                 rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
         }
-        // work items: TX x TY columns, z split into chunks
-        const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
-        const int zc = dim == 3 ? choose_zchunk((long long)tx * ty, d.nz) : 1;
-        for (int z0 = 0; z0 < d.nz; z0 += zc)
-            for (int by = 0; by < ty; ++by)
-                for (int bx = 0; bx < tx; ++bx) {
-                    WorkItem w;
-                    w.dom = k;
-                    w.x0 = bx * TX;
-                    w.y0 = by * TY;
-                    w.z0 = z0;
-                    w.z1 = z0 + zc < d.nz ? z0 + zc : d.nz;
-                    w.pad = 0;
-                    items.push_back(w);
-                }
+    }
+    // Persistent launch: as many blocks as fit on the GPU at once, taking work
+    // items dynamically.  Items are columns of TX x TY sites over z-segments of
+    // about kSegment planes, listed segment by segment so that concurrently
+    // running items are neighbours at similar heights.
+    if (rc == LBPF_OK) {
+        c->smem = L->step_smem();
+        cudaError_t e = L->prepare(c->smem);
+        if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
     }
     if (rc == LBPF_OK) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
+        const long long G0 = (long long)L->blocks_per_sm(c->smem) * sms;
+        // z-segment length: balances the per-item prologue (two extra planes)
+        // against the tail of the dynamic schedule, L ~ sqrt(5 units / blocks)
+        long long units = 0;
+        for (int k = 0; k < n_domains; ++k) {
+            const lbpf_domain& d = domains[k];
+            units += (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz;
+        }
+        int kSegment = LBPF_SEGMENT > 0 ? LBPF_SEGMENT : (int)std::lround(std::sqrt(5.0 * (double)units / (double)G0));
+        if (kSegment < 8) kSegment = 8;
+        if (kSegment > 256) kSegment = 256;
+        for (int k = 0; k < n_domains; ++k) {
+            const lbpf_domain& d = domains[k];
+            const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
+            const int nseg = (d.nz + kSegment - 1) / kSegment;
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int z0 = (int)((long long)sg * d.nz / nseg), z1 = (int)((long long)(sg + 1) * d.nz / nseg);
+                for (int by = 0; by < ty; ++by)
+                    for (int bx = 0; bx < tx; ++bx) {
+                        WorkItem w;
+                        w.dom = k;
+                        w.x0 = bx * TX;
+                        w.y0 = by * TY;
+                        w.z0 = z0;
+                        w.z1 = z1;
+                        w.pad = 0;
+                        items.push_back(w);
+                    }
+            }
+        }
+        long long G = G0;
+        if (G > (long long)items.size()) G = (long long)items.size();
+        c->n_blocks = (int)G;
         c->n_items = (int)items.size();
         rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_items), sizeof(WorkItem) * items.size());
+        if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 2);
+        if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
+            rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
     }
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_dd), sizeof(DomainDev) * n_domains);
     if (rc == LBPF_OK) {
@@ -251,11 +275,6 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
             cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomainDev) * n_domains, cudaMemcpyHostToDevice, c->stream) !=
                 cudaSuccess)
             rc = fail(c, LBPF_ECUDA, "lbpf_create: copying the domain table failed");
-    }
-    if (rc == LBPF_OK) {
-        c->smem = L->step_smem();
-        cudaError_t e = L->prepare(c->smem);
-        if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
     }
     if (rc == LBPF_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(c, LBPF_ECUDA, "lbpf_create: stream synchronisation failed");
@@ -358,12 +377,14 @@ extern "C" int lbpf_step(lbpf_ctx* c, int n_steps)
         StepArgs a;
         a.doms = c->d_dd;
         a.items = c->d_items;
+        a.n_items = c->n_items;
+        a.counters = c->d_counters;
         a.cur = c->cur;
         a.fcur = c->fcur;
         a.acur = c->acur;
         a.collide = c->lagged;
         a.grad = c->grad;
-        CK(c->L->step(a, c->n_items, c->smem, c->stream));
+        CK(c->L->step(a, c->n_blocks, c->smem, c->stream));
         c->cur ^= 1;
         c->acur ^= 1;
         if (c->lagged) c->fcur ^= 1;

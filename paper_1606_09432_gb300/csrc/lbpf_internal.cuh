@@ -173,6 +173,8 @@ struct WorkItem {
 struct StepArgs {
     const DomainDev* doms;
     const WorkItem* items;
+    int n_items;
+    int* counters;         // two work counters, used alternately (see step_kernel)
     int cur;    // g / phi / I buffer holding time n (new = cur ^ 1)
     int fcur;   // f buffer read (f^{n-1} when collide, f^n when load)
     int acur;   // aux buffer read (new = acur ^ 1)
@@ -180,9 +182,28 @@ struct StepArgs {
     int grad;   // LBPF_GRAD_DD / LBPF_GRAD_FD
 };
 
+// Tile of one thread block of the step kernel: TX x TY sites per z-plane,
+// one thread per site of the tile.
+#ifndef LBPF_TY
+#define LBPF_TY 8
+#endif
 constexpr int TX = 32;
-constexpr int TY = 8;
+constexpr int TY = LBPF_TY;
 constexpr int NT = TX * TY;
+
+// Index of the direction opposite to i on lattice L.
+template <class L>
+LBPF_HD constexpr int opposite(int i)
+{
+    for (int j = 0; j < L::Q; ++j)
+        if (L::ex(j) == -L::ex(i) && L::ey(j) == -L::ey(i) && L::ez(j) == -L::ez(i)) return j;
+    return -1;
+}
+
+// 1/x: IEEE division in FP64; the hardware reciprocal (2 ulp) in FP32.
+template <class R> __device__ __forceinline__ R recip(R x);
+template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
 
 // ---------------------------------------------------------------------------
 // Anisotropy: a_s and N for a lattice-unit gradient G.  Written with the unit
@@ -273,10 +294,12 @@ __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz
 // ---------------------------------------------------------------------------
 struct Launchers {
     // Fused step over all work items.
-    cudaError_t (*step)(const StepArgs& a, int n_items, size_t smem, cudaStream_t s);
+    cudaError_t (*step)(const StepArgs& a, int n_blocks, size_t smem, cudaStream_t s);
     size_t (*step_smem)();
     // Opt the step kernel into `smem` bytes of dynamic shared memory.
     cudaError_t (*prepare)(size_t smem);
+    // Resident blocks per SM of the step kernel with `smem` bytes.
+    int (*blocks_per_sm)(size_t smem);
     // Heat step alone, lagged -> synced state of one domain (f^{n-1}, aux^{n-1},
     // phi^n -> f^n [+ aux^n]).
     cudaError_t (*heat_sync)(const DomainDev* d, int cur, int fcur, int acur, cudaStream_t s);

@@ -37,8 +37,68 @@
 
 namespace lbpf {
 
+// Minimum resident blocks per SM requested from the compiler (register cap:
+// 4 blocks of 256 threads leave 64 registers per thread).
+#ifndef LBPF_STEP_MINB
+#define LBPF_STEP_MINB 4
+#endif
+
+// Collision coefficients of one site, (c1, c2, s, vx, vy, vz), in one plane
+// slot of 6 * CP values.  FP32: an array of float4 (c1, c2, s, vx) followed by
+// an array of float2 (vy, vz), so that a direction reads one or two vectors;
+// FP64: six scalar arrays.
+template <class R> struct CoefIO;
+template <> struct CoefIO<float> {
+    __device__ static void store(float* pl, int CP, int ci, float c1, float c2, float s, float vx, float vy, float vz)
+    {
+        reinterpret_cast<float4*>(pl)[ci] = make_float4(c1, c2, s, vx);
+        reinterpret_cast<float2*>(pl + 4 * CP)[ci] = make_float2(vy, vz);
+    }
+    __device__ static void load(const float* pl, int CP, int ci, bool need_yz, float& c1, float& c2, float& s,
+                                float& vx, float& vy, float& vz)
+    {
+        const float4 a = reinterpret_cast<const float4*>(pl)[ci];
+        c1 = a.x;
+        c2 = a.y;
+        s = a.z;
+        vx = a.w;
+        vy = vz = 0.f;
+        if (need_yz) {
+            const float2 b = reinterpret_cast<const float2*>(pl + 4 * CP)[ci];
+            vy = b.x;
+            vz = b.y;
+        }
+    }
+};
+template <> struct CoefIO<double> {
+    __device__ static void store(double* pl, int CP, int ci, double c1, double c2, double s, double vx, double vy,
+                                 double vz)
+    {
+        pl[ci] = c1;
+        pl[CP + ci] = c2;
+        pl[2 * CP + ci] = s;
+        pl[3 * CP + ci] = vx;
+        pl[4 * CP + ci] = vy;
+        pl[5 * CP + ci] = vz;
+    }
+    __device__ static void load(const double* pl, int CP, int ci, bool need_yz, double& c1, double& c2, double& s,
+                                double& vx, double& vy, double& vz)
+    {
+        c1 = pl[ci];
+        c2 = pl[CP + ci];
+        s = pl[2 * CP + ci];
+        vx = pl[3 * CP + ci];
+        vy = vz = 0.0;
+        if (need_yz) {
+            vy = pl[4 * CP + ci];
+            vz = pl[5 * CP + ci];
+        }
+    }
+};
+
+// One work item: the column (x0, y0) of one domain over planes [z0, z1).
 template <class PL, class UL, class S>
-__global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
+__device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
     using R = typename S::Real;
     using T = typename S::T;
@@ -48,19 +108,17 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
     constexpr int NPH = D == 3 ? 4 : 1;                     // phi / index ring depth
     constexpr int NH = D == 3 ? 3 : 1;                      // h ring depth
     constexpr int NC = D == 3 ? 3 : 1;                      // coefficient ring depth
-    constexpr int NCO = D + 3;                              // c1, c2, s, v[D]
+    constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
     constexpr int QG = PL::Q, QU = UL::Q;
     constexpr bool DEV = S::dev;
     (void)RY;
     (void)CY;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_phi = reinterpret_cast<R*>(smem_raw);
     R* s_h = s_phi + NPH * RP;
     R* s_co = s_h + NH * RP;
     int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * NCO * CP);
 
-    const WorkItem it = args.items[blockIdx.x];
     const DomainDev& dm = args.doms[it.dom];
     const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
     const long long n = dm.n;
@@ -193,9 +251,12 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
             // gradient of phi^n (Sec. 4.2)
             R Gx = 0, Gy = 0, Gz = 0;
             if (args.grad == LBPF_GRAD_DD) {
-                // Eq. (Def_DeriveeDirectionnelle) and Eq. (Grad_DF-Centree)
+                // Eq. (Def_DeriveeDirectionnelle) and Eq. (Grad_DF-Centree); a
+                // direction and its opposite give the same term, so each pair is
+                // taken once with twice the weight.
 #pragma unroll
                 for (int i = 1; i < QG; ++i) {
+                    if (i > opposite<PL>(i)) continue;
                     const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
                     const R dd = s_phi[sphi(zp + ez) * RP + (py + ey) * RX + (px + ex)] -
                                  s_phi[sphi(zp - ez) * RP + (py - ey) * RX + (px - ex)];
@@ -204,7 +265,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
                     if (ey) Gy += R(ey) * wd;
                     if (ez) Gz += R(ez) * wd;
                 }
-                const R k = R(0.5 / PL::E2);
+                const R k = R(1.0 / PL::E2);
                 Gx *= k;
                 Gy *= k;
                 Gz *= k;
@@ -238,18 +299,13 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
             if (cryst > 0 && cryst <= dm.n_crystals) anisotropy<R, D>(dm.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
 
             const R A2 = a * a;
-            const R iA2 = R(1) / A2;
-            const R ieta = R(1) / (A2 * De2 + R(0.5));
+            const R iA2 = recip<R>(A2);
+            const R ieta = recip<R>(A2 * De2 + R(0.5));
             const R omp = (R(1) - ph) * (R(1) + ph);
             const R Qphi = (ph - lam * u * omp) * omp;
             const R vf = -De2 * ieta * iA2;
-            const int ci = ly * CX + lx;
-            dco[0 * CP + ci] = (R(1) - ieta) * iA2;
-            dco[1 * CP + ci] = iA2 - R(1);
-            dco[2 * CP + ci] = (ph * ieta + qphi * Qphi) * iA2;
-            dco[3 * CP + ci] = vf * Nx;
-            dco[4 * CP + ci] = vf * Ny;
-            if (D == 3) dco[5 * CP + ci] = vf * Nz;
+            CoefIO<R>::store(dco, CP, ly * CX + lx, (R(1) - ieta) * iA2, iA2 - R(1), (ph * ieta + qphi * Qphi) * iA2,
+                             vf * Nx, vf * Ny, vf * Nz);
         }
     };
 
@@ -294,7 +350,9 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
 #pragma unroll
         for (int i = 0; i < QG; ++i) {
             const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
-            const R* co = s_co + sco(z - ez) * NCO * CP + (cy - ey) * CX + (cx - ex);
+            R c1, c2, cs, vx, vy, vz;
+            CoefIO<R>::load(s_co + sco(z - ez) * NCO * CP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
+                            cs, vx, vy, vz);
             R gp;
             if (i == 0) {
                 gp = gl[0];
@@ -305,10 +363,10 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
                 gp = R(PL::w(i)) * phs + to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
             }
             R ev = R(0);
-            if (ex) ev += R(ex) * co[3 * CP];
-            if (ey) ev += R(ey) * co[4 * CP];
-            if (D == 3 && ez) ev += R(ez) * co[5 * CP];
-            const R v = co[0] * gp - co[CP] * gl[i] + R(PL::w(i)) * (co[2 * CP] + ev);
+            if (ex) ev += R(ex) * vx;
+            if (ey) ev += R(ey) * vy;
+            if (D == 3 && ez) ev += R(ez) * vz;
+            const R v = c1 * gp - c2 * gl[i] + R(PL::w(i)) * (cs + ev);
             gnew[i] = v;
             phinew += v;
         }
@@ -351,13 +409,36 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs args)
     }
 }
 
+// Persistent launch with dynamic scheduling: as many blocks as fit on the GPU
+// take work items in list order from a counter.  The host orders the items
+// z-segment by z-segment, so that the blocks running at any moment hold
+// neighbouring columns at similar heights and their halo rims are served by L2.
+// The launch uses counter[cur] and clears counter[cur ^ 1] for the next step
+// (launches on one stream run in order; cur alternates every step).
+template <class PL, class UL, class S>
+__global__ void __launch_bounds__(NT, LBPF_STEP_MINB) step_kernel(const StepArgs args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_next;
+    int* counter = args.counters + args.cur;
+    if (blockIdx.x == 0 && threadIdx.x == 0) args.counters[args.cur ^ 1] = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int k = s_next;
+        if (k >= args.n_items) break;
+        step_item<PL, UL, S>(args, args.items[k], smem_raw);
+        __syncthreads();
+    }
+}
+
 template <class PL, class UL, class S>
 constexpr size_t step_smem_bytes()
 {
     using R = typename S::Real;
     constexpr int D = PL::D;
     constexpr int RP = (TX + 4) * (TY + 4), CP = (TX + 2) * (TY + 2);
-    constexpr int NPH = D == 3 ? 4 : 1, NH = D == 3 ? 3 : 1, NC = D == 3 ? 3 : 1, NCO = D + 3;
+    constexpr int NPH = D == 3 ? 4 : 1, NH = D == 3 ? 3 : 1, NC = D == 3 ? 3 : 1, NCO = 6;
     return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (size_t)NPH * RP;
 }
 

@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbpf.so")
+LIB_PATH = os.environ.get("LBPF_LIB") or os.path.join(_HERE, "liblbpf.so")
 
 # enums (include/lbpf.h)
 LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_ETIMEOUT, LBPF_ENONFINITE, LBPF_ERANGE = 0, -1, -2, -3, -4, -5, -6
