@@ -38,6 +38,9 @@ WORKLOADS = {
     "c3-512-bf16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with BF16 deviation storage, "
                        "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 3, 512),
     "c3-512-fp32": ("3D 512^3 periodic, D3Q15/D3Q7, FP32, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 1, 512),
+    "c4-batch64-fp32": ("batched 2D multi-crystal: 64 periodic domains, sides U{128..1024} (24.4 M sites), D2Q9/D2Q5, "
+                        "FP32, 1-12 seeds each with its own angle-form crystal (q=4, theta, eps), Delta per domain, "
+                        "one launch per step, CUDA graphs", 0, 1, 0),
 }
 DTYPE = {0: "f64", 1: "f32", 2: "f32 arithmetic, f16 storage", 3: "f32 arithmetic, bf16 storage"}
 METRIC = "fused phi+u LB step MLUPS"
@@ -133,7 +136,25 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def make_batch(L, W, stream, precision=1):
+    doms, seeds = [], []
+    for w in W.c4():
+        prm = dict(w["params"])
+        lam = prm.pop("lam")
+        _, L_, _ = w["shape"][0], w["shape"][1], w["shape"][2]
+        crs = [L.make_crystal(**c) for c in w["crystals"]]
+        doms.append(L.make_domain(L_, L_, 1, lam=lam, crystals=crs, **prm))
+        seeds.append(w["seeds"])
+    s = L.Solver(doms, L.LBPF_D2Q9_D2Q5, L.LBPF_GRAD_DD, precision, stream=stream)
+    for k, sd in enumerate(seeds):
+        s.seed(sd, domain=k)
+    c = seeds[0][0]
+    return s, {"centre": (int(c[0]), int(c[1]), 0)}
+
+
 def make_solver(L, W, workload, stream, size=0):
+    if workload.startswith("c4"):
+        return make_batch(L, W, stream)
     desc, lattice, precision, n = WORKLOADS[workload]
     n = size or n
     w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
@@ -271,7 +292,7 @@ def main():
     # end to end through the public API with host buffers: write the initial
     # fields from pinned host memory, advance K steps, read phi and u back.
     e2e = None
-    if True:
+    if not args.workload.startswith("c4"):
         shape = s.shape()
         tdt = torch.float64 if precision == L.LBPF_FP64 else torch.float32
         phi_h = torch.empty(shape, dtype=tdt).pin_memory()
@@ -308,7 +329,7 @@ def main():
     achieved = bps * sites / avg_kernel_s / 1e9
     traffic = profiled_traffic(args.workload)
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not args.workload.startswith("c4"):
         v, st, el = cpu_oracle_rate(args.workload, args.cpu_budget, n=96)
         cpu = {"value": round(v, 3), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"96^3 periodic crop of the workload, {st} FP64 oracle steps in {el:.1f} s"}
@@ -327,6 +348,8 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "check": {"tip_x": round(float(tip[0]), 4), "solid_fraction": sf, "conserved": cons},
+        "schedule": {"tile_rows": s.query(L.LBPF_Q_TILE_ROWS), "segment": s.query(L.LBPF_Q_SEGMENT),
+                     "blocks": s.query(L.LBPF_Q_BLOCKS)},
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -164,9 +164,12 @@ int lbpf_write_fields(lbpf_ctx* ctx, int domain, const void* phi, const void* u,
 
 /* Advance every domain by n_steps time steps (n_steps >= 0).  One step is
  * the phase-field scheme of Sec. 3.2 followed by the heat scheme of Sec. 3.1
- * with Q_u = (phi(t + dt) - phi(t)) / (2 dt).  Asynchronous on the
- * context's stream; launch errors are returned, device errors surface at the
- * next synchronising call. */
+ * with Q_u = (phi(t + dt) - phi(t)) / (2 dt), one kernel launch for all
+ * domains.  On a non-default stream, runs of 16 steps are replayed from CUDA
+ * graphs captured on first use (do not call lbpf_step while another capture
+ * is active on the context's stream).  Asynchronous on the context's stream;
+ * launch errors are returned, device errors surface at the next
+ * synchronising call. */
 int lbpf_step(lbpf_ctx* ctx, int n_steps);
 
 typedef enum {
@@ -211,8 +214,19 @@ typedef enum {
     LBPF_Q_BYTES_PER_SITE = 2, /* algorithmic HBM bytes one fused step moves per site */
     LBPF_Q_DEVICE_BYTES = 3,   /* device memory held by the context                  */
     LBPF_Q_LAMBDA = 4,         /* lambda of domain 0 (after the lambda* rule)        */
-    LBPF_Q_STEP_KERNELS = 5    /* kernel launches issued by lbpf_step so far          */
+    LBPF_Q_STEP_KERNELS = 5,   /* step-kernel launches issued by lbpf_step so far     */
+    LBPF_Q_TILE_ROWS = 6,      /* rows of the step kernel's tile (autotuned)          */
+    LBPF_Q_SEGMENT = 7,        /* z-planes per work item of the step kernel (3D)      */
+    LBPF_Q_BLOCKS = 8          /* resident blocks of the persistent step launch       */
 } lbpf_query_t;
+
+/* Override the work schedule of the step kernel (normally chosen at
+ * lbpf_create by a cached or timed autotune, or by rule): tile_rows is 8 or 16
+ * (sites of a tile along y; tiles are 32 sites along x), segment the number of
+ * z-planes per work item (3D; >= 1, ignored in 2D).  Results do not depend on
+ * the schedule; only speed does.  A performance knob with no counterpart in
+ * the paper.  Errors: LBPF_EINVAL. */
+int lbpf_set_schedule(lbpf_ctx* ctx, int tile_rows, int segment);
 
 /* Read a property of the context into *value. */
 int lbpf_query(const lbpf_ctx* ctx, int what, double* value);

@@ -87,7 +87,8 @@ __global__ void equilibrate_kernel(const DomainDev* dp, int cur, int fcur, int a
         int cryst = 1;
         if (d.use_index) {
             int Iv = I[s];
-            if (finalize_index && !(ph > R(0) || Gx * Gx + Gy * Gy + Gz * Gz > R(d.xi_lu * d.xi_lu))) Iv = 0;
+            const double xi = sizeof(R) == 4 ? fmax(d.xi_lu, 1e-6) : d.xi_lu;
+            if (finalize_index && !(ph > R(0) || Gx * Gx + Gy * Gy + Gz * Gz > R(xi * xi))) Iv = 0;
             I[s] = (int8_t)Iv;
             cryst = Iv;
         }
@@ -225,20 +226,36 @@ inline int grid_for(long long n)
 
 template <class PL, class UL, class S>
 struct LauncherImpl {
-    static cudaError_t step(const StepArgs& a, int n_blocks, size_t smem, cudaStream_t s)
+    template <int TY>
+    static cudaError_t step_v(const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        step_kernel<PL, UL, S><<<n_blocks, NT, smem, s>>>(a);
+        step_kernel<PL, UL, S, TY><<<n_blocks, TX * TY, step_smem_bytes<PL, UL, S, TY>(), s>>>(a);
         return cudaGetLastError();
     }
-    static size_t smem() { return step_smem_bytes<PL, UL, S>(); }
-    static cudaError_t prepare(size_t bytes)
+    static cudaError_t step(int v, const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        return cudaFuncSetAttribute(step_kernel<PL, UL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        return v == 0 ? step_v<kTileRows[0]>(a, n_blocks, s) : step_v<kTileRows[1]>(a, n_blocks, s);
     }
-    static int blocks_per_sm(size_t bytes)
+    static size_t smem(int v)
+    {
+        return v == 0 ? step_smem_bytes<PL, UL, S, kTileRows[0]>() : step_smem_bytes<PL, UL, S, kTileRows[1]>();
+    }
+    static cudaError_t prepare(int v)
+    {
+        if (v == 0)
+            return cudaFuncSetAttribute(step_kernel<PL, UL, S, kTileRows[0]>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(0));
+        return cudaFuncSetAttribute(step_kernel<PL, UL, S, kTileRows[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem(1));
+    }
+    static int blocks_per_sm(int v)
     {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<PL, UL, S>, NT, bytes) != cudaSuccess) {
+        cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                     &nb, step_kernel<PL, UL, S, kTileRows[0]>, TX * kTileRows[0], smem(0))
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                     &nb, step_kernel<PL, UL, S, kTileRows[1]>, TX * kTileRows[1], smem(1));
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return 1;
         }

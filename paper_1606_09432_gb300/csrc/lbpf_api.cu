@@ -37,7 +37,12 @@ struct lbpf_ctx {
     DomainDev* d_dd = nullptr;
     WorkItem* d_items = nullptr;
     int* d_counters = nullptr;
-    int n_items = 0, n_blocks = 0;
+    int n_items = 0, n_blocks = 0, items_cap = 0;
+    int tile_v = 0, seg_len = 0, sms = 1;
+    // graphs of kGraphSteps steady-state launches, keyed by (cur, fcur, acur)
+    cudaGraphExec_t graphs[8] = {};
+    bool graphs_off = false;
+    std::string tuned;  // how the schedule was chosen
     cudaStream_t stream = nullptr;
     int device = 0;
     const Launchers* L = nullptr;
@@ -107,6 +112,180 @@ static void free_all(lbpf_ctx* c)
     c->allocs.clear();
 }
 
+
+// ---------------------------------------------------------------------------
+// Work schedule of the step kernel.  Items are columns of TX x TY sites over
+// z-segments, listed segment by segment; the kernel runs as many blocks as
+// fit on the GPU and takes items in order (see step_kernel).
+// ---------------------------------------------------------------------------
+static long long column_units(const lbpf_ctx* c, int ty)
+{
+    long long units = 0;
+    for (const DomainDev& d : c->dd) units += (long long)((d.nx + TX - 1) / TX) * ((d.ny + ty - 1) / ty) * d.nz;
+    return units;
+}
+
+// Segment length balancing the per-item prologue (two extra planes) against
+// the tail of the dynamic schedule: L ~ sqrt(5 units / resident blocks).
+static int default_segment(const lbpf_ctx* c, int v)
+{
+    if (LBPF_SEGMENT > 0) return LBPF_SEGMENT;
+    const double G = (double)c->L->blocks_per_sm(v) * c->sms;
+    int L = (int)std::lround(std::sqrt(5.0 * (double)column_units(c, kTileRows[v]) / G));
+    return L < 8 ? 8 : (L > 256 ? 256 : L);
+}
+
+static int set_schedule(lbpf_ctx* c, int v, int seg)
+{
+    const int ty = kTileRows[v];
+    std::vector<WorkItem> items;
+    for (int k = 0; k < c->n_domains; ++k) {
+        const DomainDev& d = c->dd[k];
+        const int tx = (d.nx + TX - 1) / TX, tyn = (d.ny + ty - 1) / ty;
+        const int nseg = c->dim == 3 ? (d.nz + seg - 1) / seg : 1;
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int z0 = (int)((long long)sg * d.nz / nseg), z1 = (int)((long long)(sg + 1) * d.nz / nseg);
+            for (int by = 0; by < tyn; ++by)
+                for (int bx = 0; bx < tx; ++bx) {
+                    WorkItem w;
+                    w.dom = k;
+                    w.x0 = bx * TX;
+                    w.y0 = by * ty;
+                    w.z0 = z0;
+                    w.z1 = z1;
+                    w.pad = 0;
+                    items.push_back(w);
+                }
+        }
+    }
+    if ((int)items.size() > c->items_cap) {
+        int rc;
+        void* p = nullptr;
+        if ((rc = dev_alloc(c, &p, sizeof(WorkItem) * items.size()))) return rc;
+        c->d_items = static_cast<WorkItem*>(p);  // the old table stays in the context's allocation list
+        c->items_cap = (int)items.size();
+    }
+    CK(cudaMemcpyAsync(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->n_items = (int)items.size();
+    long long G = (long long)c->L->blocks_per_sm(v) * c->sms;
+    c->n_blocks = (int)(G < c->n_items ? G : c->n_items);
+    c->tile_v = v;
+    c->seg_len = seg;
+    for (cudaGraphExec_t& g : c->graphs)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return LBPF_OK;
+}
+
+static std::string tune_key(const lbpf_ctx* c)
+{
+    char buf[160];
+    unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the domain sizes
+    for (const DomainDev& d : c->dd)
+        for (int v : {d.nx, d.ny, d.nz, d.use_index}) {
+            h ^= (unsigned long long)(unsigned)v;
+            h *= 1099511628211ULL;
+        }
+    snprintf(buf, sizeof(buf), "lat%d-prec%d-grad%d-dom%d-%016llx-sm%d", c->lattice, c->precision, c->grad,
+             c->n_domains, h, c->sms);
+    return buf;
+}
+
+static std::string tune_cache_path()
+{
+    const char* p = getenv("LBPF_TUNE_CACHE");
+    if (p) return p;
+    const char* home = getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/lbpf_tune.txt";
+}
+
+// Time a few launches of the current schedule (on the zero state).
+static double time_schedule(lbpf_ctx* c, int launches)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30;
+    }
+    StepArgs a;
+    a.doms = c->d_dd;
+    a.items = c->d_items;
+    a.n_items = c->n_items;
+    a.counters = c->d_counters;
+    a.fcur = a.acur = 0;
+    a.collide = 1;
+    a.grad = c->grad;
+    double best = 1e30;
+    for (int k = 0; k < launches + 2; ++k) {
+        a.cur = k & 1;
+        cudaEventRecord(e0, c->stream);
+        if (c->L->step(c->tile_v, a, c->n_blocks, c->stream) != cudaSuccess) break;
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (k >= 2 && ms < best) best = ms;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+// Pick the tile variant and segment length: from the cache file, else by
+// timing the candidates on large contexts (the state is all zeros at this
+// point and stays zero: every update of a zero state is zero), else by rule.
+static int choose_schedule(lbpf_ctx* c)
+{
+    const std::string key = tune_key(c);
+    const std::string path = tune_cache_path();
+    if (FILE* f = fopen(path.c_str(), "r")) {
+        char k[200];
+        int v, seg;
+        while (fscanf(f, "%199s %d %d", k, &v, &seg) == 3)
+            if (key == k && v >= 0 && v < kNumTileVariants && seg >= 1) {
+                fclose(f);
+                c->tuned = "cache";
+                return set_schedule(c, v, seg);
+            }
+        fclose(f);
+    }
+    double sites = 0;
+    for (const DomainDev& d : c->dd) sites += (double)d.n;
+    const char* env = getenv("LBPF_AUTOTUNE");
+    const bool tune = env ? atoi(env) != 0 : sites >= 4e6;
+    int best_v = c->dim == 3 ? 0 : 1, best_seg = default_segment(c, best_v);
+    if (tune) {
+        double best_t = 1e30;
+        for (int v = 0; v < kNumTileVariants; ++v) {
+            const int L0 = default_segment(c, v);
+            const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
+            for (int j = 0; j < (c->dim == 3 ? 3 : 1); ++j) {
+                int rc = set_schedule(c, v, segs[j]);
+                if (rc) return rc;
+                const double t = time_schedule(c, 4);
+                if (t < best_t) {
+                    best_t = t;
+                    best_v = v;
+                    best_seg = segs[j];
+                }
+            }
+        }
+        CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream));
+        c->tuned = "timed";
+        if (FILE* f = fopen(path.c_str(), "a")) {
+            fprintf(f, "%s %d %d\n", key.c_str(), best_v, best_seg);
+            fclose(f);
+        }
+    } else {
+        c->tuned = "rule";
+    }
+    return set_schedule(c, best_v, best_seg);
+}
+
 extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattice, int grad, int precision,
                            void* stream, lbpf_ctx** out)
 {
@@ -168,7 +347,6 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
 
     int rc = LBPF_OK;
     long long max_n = 0;
-    std::vector<WorkItem> items;
     c->dd.resize(n_domains);
     for (int k = 0; k < n_domains && rc == LBPF_OK; ++k) {
         const lbpf_domain& d = domains[k];
@@ -212,57 +390,17 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
                 rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
         }
     }
-    // Persistent launch: as many blocks as fit on the GPU at once, taking work
-    // items dynamically.  Items are columns of TX x TY sites over z-segments of
-    // about kSegment planes, listed segment by segment so that concurrently
-    // running items are neighbours at similar heights.
     if (rc == LBPF_OK) {
-        c->smem = L->step_smem();
-        cudaError_t e = L->prepare(c->smem);
-        if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
-    }
-    if (rc == LBPF_OK) {
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
-        const long long G0 = (long long)L->blocks_per_sm(c->smem) * sms;
-        // z-segment length: balances the per-item prologue (two extra planes)
-        // against the tail of the dynamic schedule, L ~ sqrt(5 units / blocks)
-        long long units = 0;
-        for (int k = 0; k < n_domains; ++k) {
-            const lbpf_domain& d = domains[k];
-            units += (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz;
+        if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
+            c->sms = 1;
+        for (int v = 0; v < kNumTileVariants && rc == LBPF_OK; ++v) {
+            cudaError_t e = L->prepare(v);
+            if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
         }
-        int kSegment = LBPF_SEGMENT > 0 ? LBPF_SEGMENT : (int)std::lround(std::sqrt(5.0 * (double)units / (double)G0));
-        if (kSegment < 8) kSegment = 8;
-        if (kSegment > 256) kSegment = 256;
-        for (int k = 0; k < n_domains; ++k) {
-            const lbpf_domain& d = domains[k];
-            const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
-            const int nseg = (d.nz + kSegment - 1) / kSegment;
-            for (int sg = 0; sg < nseg; ++sg) {
-                const int z0 = (int)((long long)sg * d.nz / nseg), z1 = (int)((long long)(sg + 1) * d.nz / nseg);
-                for (int by = 0; by < ty; ++by)
-                    for (int bx = 0; bx < tx; ++bx) {
-                        WorkItem w;
-                        w.dom = k;
-                        w.x0 = bx * TX;
-                        w.y0 = by * TY;
-                        w.z0 = z0;
-                        w.z1 = z1;
-                        w.pad = 0;
-                        items.push_back(w);
-                    }
-            }
-        }
-        long long G = G0;
-        if (G > (long long)items.size()) G = (long long)items.size();
-        c->n_blocks = (int)G;
-        c->n_items = (int)items.size();
-        rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_items), sizeof(WorkItem) * items.size());
-        if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 2);
-        if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
-            rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
     }
+    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 2);
+    if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
+        rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_dd), sizeof(DomainDev) * n_domains);
     if (rc == LBPF_OK) {
         c->scratch_bytes = (size_t)max_n * (c->rsize > 4 ? c->rsize : 4);
@@ -270,14 +408,13 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
     }
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), sizeof(double) * (3 * kReduceBlocks + 16));
     if (rc == LBPF_OK) {
-        if (cudaMemcpyAsync(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomainDev) * n_domains, cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess)
+        if (cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomainDev) * n_domains, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
             rc = fail(c, LBPF_ECUDA, "lbpf_create: copying the domain table failed");
     }
     if (rc == LBPF_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(c, LBPF_ECUDA, "lbpf_create: stream synchronisation failed");
+    if (rc == LBPF_OK) rc = choose_schedule(c);
     if (rc != LBPF_OK) {
         t_err = c->err;
         free_all(c);
@@ -368,29 +505,87 @@ extern "C" int lbpf_write_fields(lbpf_ctx* c, int domain, const void* phi, const
     return LBPF_OK;
 }
 
+// One launch of the fused step on the context's stream.
+static int launch_step(lbpf_ctx* c)
+{
+    StepArgs a;
+    a.doms = c->d_dd;
+    a.items = c->d_items;
+    a.n_items = c->n_items;
+    a.counters = c->d_counters;
+    a.cur = c->cur;
+    a.fcur = c->fcur;
+    a.acur = c->acur;
+    a.collide = c->lagged;
+    a.grad = c->grad;
+    CK(c->L->step(c->tile_v, a, c->n_blocks, c->stream));
+    c->cur ^= 1;
+    c->acur ^= 1;
+    if (c->lagged) c->fcur ^= 1;
+    c->lagged = 1;
+    c->steps += 1;
+    c->kernels += 1;
+    return LBPF_OK;
+}
+
+// Steady-state launches come in batches of kGraphSteps replayed from a CUDA
+// graph; the launch arguments of a batch depend only on the buffer parities
+// (cur, fcur, acur), which return to their start after an even batch.
+constexpr int kGraphSteps = 16;
+
+static int graph_batch(lbpf_ctx* c)
+{
+    const int key = c->cur | (c->fcur << 1) | (c->acur << 2);
+    cudaGraphExec_t& ex = c->graphs[key];
+    if (!ex) {
+        const int cur = c->cur, fcur = c->fcur, acur = c->acur;
+        const long long steps = c->steps, kernels = c->kernels;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = true;
+            return LBPF_OK;
+        }
+        int rc = LBPF_OK;
+        for (int k = 0; k < kGraphSteps && rc == LBPF_OK; ++k) rc = launch_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->cur = cur;  // capture recorded the launches without running them
+        c->fcur = fcur;
+        c->acur = acur;
+        c->steps = steps;
+        c->kernels = kernels;
+        if (rc != LBPF_OK || e != cudaSuccess || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            ex = nullptr;
+            c->graphs_off = true;
+            return LBPF_OK;
+        }
+        cudaGraphDestroy(g);
+    }
+    CK(cudaGraphLaunch(ex, c->stream));
+    c->steps += kGraphSteps;
+    c->kernels += kGraphSteps;  // each batch is kGraphSteps step-kernel launches
+    return LBPF_OK;
+}
+
 extern "C" int lbpf_step(lbpf_ctx* c, int n_steps)
 {
     int rc = check_ctx(c, 0);
     if (rc) return rc;
     if (n_steps < 0) return fail(c, LBPF_EINVAL, "lbpf_step: n_steps < 0");
-    for (int k = 0; k < n_steps; ++k) {
-        StepArgs a;
-        a.doms = c->d_dd;
-        a.items = c->d_items;
-        a.n_items = c->n_items;
-        a.counters = c->d_counters;
-        a.cur = c->cur;
-        a.fcur = c->fcur;
-        a.acur = c->acur;
-        a.collide = c->lagged;
-        a.grad = c->grad;
-        CK(c->L->step(a, c->n_blocks, c->smem, c->stream));
-        c->cur ^= 1;
-        c->acur ^= 1;
-        if (c->lagged) c->fcur ^= 1;
-        c->lagged = 1;
-        c->steps += 1;
-        c->kernels += 1;
+    // graphs need a capturable stream (not the legacy default stream)
+    const bool graphs = c->stream != nullptr && !c->graphs_off;
+    while (n_steps > 0) {
+        if (graphs && c->lagged && n_steps >= kGraphSteps && !c->graphs_off) {
+            if ((rc = graph_batch(c))) return rc;
+            if (!c->graphs_off) {
+                n_steps -= kGraphSteps;
+                continue;
+            }
+        }
+        if ((rc = launch_step(c))) return rc;
+        n_steps -= 1;
     }
     return LBPF_OK;
 }
@@ -478,6 +673,18 @@ extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, dou
     return LBPF_OK;
 }
 
+extern "C" int lbpf_set_schedule(lbpf_ctx* c, int tile_rows, int segment)
+{
+    int rc = check_ctx(c, 0);
+    if (rc) return rc;
+    int v = -1;
+    for (int k = 0; k < kNumTileVariants; ++k)
+        if (kTileRows[k] == tile_rows) v = k;
+    if (v < 0 || segment < 1) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: tile_rows must be 8 or 16, segment >= 1");
+    CK(cudaStreamSynchronize(c->stream));
+    return set_schedule(c, v, segment);
+}
+
 extern "C" int lbpf_query(const lbpf_ctx* c, int what, double* value)
 {
     if (!c || !value) return fail(nullptr, LBPF_EINVAL, "lbpf_query: NULL argument");
@@ -490,13 +697,20 @@ extern "C" int lbpf_query(const lbpf_ctx* c, int what, double* value)
     case LBPF_Q_BYTES_PER_SITE: {
         // read + write of every stored population, of phi and of aux (and of
         // the index field when it is used)
-        v = 2.0 * (c->Sg + c->Su) * c->ssize + 4.0 * c->rsize;
-        if (c->dd[0].use_index) v += 2.0;
+        double idx_sites = 0, all_sites = 0;
+        for (const DomainDev& h : c->dd) {
+            all_sites += (double)h.n;
+            if (h.use_index) idx_sites += (double)h.n;
+        }
+        v = 2.0 * (c->Sg + c->Su) * c->ssize + 4.0 * c->rsize + 2.0 * idx_sites / all_sites;
         break;
     }
     case LBPF_Q_DEVICE_BYTES: v = (double)c->dev_bytes; break;
     case LBPF_Q_LAMBDA: v = c->dd[0].lambda; break;
     case LBPF_Q_STEP_KERNELS: v = (double)c->kernels; break;
+    case LBPF_Q_TILE_ROWS: v = kTileRows[c->tile_v]; break;
+    case LBPF_Q_SEGMENT: v = c->dim == 3 ? c->seg_len : 1; break;
+    case LBPF_Q_BLOCKS: v = c->n_blocks; break;
     default: return fail(const_cast<lbpf_ctx*>(c), LBPF_EINVAL, "lbpf_query: unknown property %d", what);
     }
     *value = v;
@@ -508,6 +722,8 @@ extern "C" int lbpf_destroy(lbpf_ctx* c)
     if (!c) return LBPF_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (cudaGraphExec_t g : c->graphs)
+        if (g) cudaGraphExecDestroy(g);
     free_all(c);
     delete c;
     return LBPF_OK;

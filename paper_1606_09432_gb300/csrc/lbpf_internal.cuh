@@ -182,14 +182,12 @@ struct StepArgs {
     int grad;   // LBPF_GRAD_DD / LBPF_GRAD_FD
 };
 
-// Tile of one thread block of the step kernel: TX x TY sites per z-plane,
-// one thread per site of the tile.
-#ifndef LBPF_TY
-#define LBPF_TY 8
-#endif
+// Tile of one thread block of the step kernel: TX x TY sites per z-plane, one
+// thread per site of the tile.  TY is a template parameter of the kernel; the
+// context picks one of kTileRows (autotuned).
 constexpr int TX = 32;
-constexpr int TY = LBPF_TY;
-constexpr int NT = TX * TY;
+constexpr int kNumTileVariants = 2;
+constexpr int kTileRows[kNumTileVariants] = {8, 16};
 
 // Index of the direction opposite to i on lattice L.
 template <class L>
@@ -293,13 +291,14 @@ __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz
 // Launchers exported by the per-lattice translation units.
 // ---------------------------------------------------------------------------
 struct Launchers {
-    // Fused step over all work items.
-    cudaError_t (*step)(const StepArgs& a, int n_blocks, size_t smem, cudaStream_t s);
-    size_t (*step_smem)();
-    // Opt the step kernel into `smem` bytes of dynamic shared memory.
-    cudaError_t (*prepare)(size_t smem);
-    // Resident blocks per SM of the step kernel with `smem` bytes.
-    int (*blocks_per_sm)(size_t smem);
+    // Fused step over all work items, tile variant v (rows kTileRows[v]).
+    cudaError_t (*step)(int v, const StepArgs& a, int n_blocks, cudaStream_t s);
+    // Dynamic shared memory of variant v.
+    size_t (*step_smem)(int v);
+    // Opt variant v into its dynamic shared memory.
+    cudaError_t (*prepare)(int v);
+    // Resident blocks per SM of variant v.
+    int (*blocks_per_sm)(int v);
     // Heat step alone, lagged -> synced state of one domain (f^{n-1}, aux^{n-1},
     // phi^n -> f^n [+ aux^n]).
     cudaError_t (*heat_sync)(const DomainDev* d, int cur, int fcur, int acur, cudaStream_t s);

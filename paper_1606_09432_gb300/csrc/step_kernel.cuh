@@ -37,12 +37,6 @@
 
 namespace lbpf {
 
-// Minimum resident blocks per SM requested from the compiler (register cap:
-// 4 blocks of 256 threads leave 64 registers per thread).
-#ifndef LBPF_STEP_MINB
-#define LBPF_STEP_MINB 4
-#endif
-
 // Collision coefficients of one site, (c1, c2, s, vx, vy, vz), in one plane
 // slot of 6 * CP values.  FP32: an array of float4 (c1, c2, s, vx) followed by
 // an array of float2 (vy, vz), so that a direction reads one or two vectors;
@@ -97,9 +91,10 @@ template <> struct CoefIO<double> {
 };
 
 // One work item: the column (x0, y0) of one domain over planes [z0, z1).
-template <class PL, class UL, class S>
+template <class PL, class UL, class S, int TY>
 __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
+    constexpr int NT = TX * TY;
     using R = typename S::Real;
     using T = typename S::T;
     constexpr int D = PL::D;
@@ -147,7 +142,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     const R lam = R(dm.lambda);
     const R ieu = R(dm.inv_eta_u);
     const R om_u = R(1) - ieu;
-    const R xi2 = R(dm.xi_lu * dm.xi_lu);
+    // index threshold; in FP32 not below the rounding noise of the gradient (1e-6)
+    const R xi2 = sizeof(R) == 4 ? R(fmax(dm.xi_lu, 1e-6) * fmax(dm.xi_lu, 1e-6)) : R(dm.xi_lu * dm.xi_lu);
     (void)Dphi;
 
     auto wrapx = [&](int v) { return v < 0 ? v + nx : (v >= nx ? v - nx : v); };
@@ -415,8 +411,9 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 // neighbouring columns at similar heights and their halo rims are served by L2.
 // The launch uses counter[cur] and clears counter[cur ^ 1] for the next step
 // (launches on one stream run in order; cur alternates every step).
-template <class PL, class UL, class S>
-__global__ void __launch_bounds__(NT, LBPF_STEP_MINB) step_kernel(const StepArgs args)
+// Launch bounds ask for 1024 resident threads per SM (64 registers a thread).
+template <class PL, class UL, class S, int TY>
+__global__ void __launch_bounds__(TX * TY, 1024 / (TX * TY)) step_kernel(const StepArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_next;
@@ -427,12 +424,12 @@ __global__ void __launch_bounds__(NT, LBPF_STEP_MINB) step_kernel(const StepArgs
         __syncthreads();
         const int k = s_next;
         if (k >= args.n_items) break;
-        step_item<PL, UL, S>(args, args.items[k], smem_raw);
+        step_item<PL, UL, S, TY>(args, args.items[k], smem_raw);
         __syncthreads();
     }
 }
 
-template <class PL, class UL, class S>
+template <class PL, class UL, class S, int TY>
 constexpr size_t step_smem_bytes()
 {
     using R = typename S::Real;

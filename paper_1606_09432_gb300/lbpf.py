@@ -22,11 +22,12 @@ LBPF_GRAD_DD, LBPF_GRAD_FD = 0, 1
 LBPF_FP64, LBPF_FP32, LBPF_FP32_FP16DEV, LBPF_FP32_BF16DEV = 0, 1, 2, 3
 LBPF_AS_CUBIC100, LBPF_AS_ANGLE, LBPF_AS_Y66, LBPF_AS_HOYT110, LBPF_AS_S111 = 0, 1, 2, 3, 4
 LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
-LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS = range(6)
+(LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS,
+ LBPF_Q_TILE_ROWS, LBPF_Q_SEGMENT, LBPF_Q_BLOCKS) = range(9)
 LBPF_MAX_CRYSTALS = 16
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
-            "lbpf_field_sums_static"]
+            "lbpf_field_sums_static", "lbpf_set_schedule"]
 
 
 class lbpf_crystal(C.Structure):
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.lbpf_last_error.argtypes = [vp]
     lib.lbpf_last_error.restype = C.c_char_p
     lib.lbpf_field_sums_static.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp]
+    lib.lbpf_set_schedule.argtypes = [vp, C.c_int, C.c_int]
     for name in EXPORTED:
         lib[name].restype = lib[name].restype if name == "lbpf_last_error" else C.c_int
     _lib = lib
@@ -170,6 +172,10 @@ def lbpf_measure(ctx, domain, cx, cy, cz=0):
     sf, cs = C.c_double(), C.c_double()
     _check(load().lbpf_measure(ctx, domain, cx, cy, cz, tip, C.byref(sf), C.byref(cs)), ctx)
     return np.array(tip[:]), sf.value, cs.value
+
+
+def lbpf_set_schedule(ctx, tile_rows, segment):
+    _check(load().lbpf_set_schedule(ctx, tile_rows, segment), ctx)
 
 
 def lbpf_query(ctx, what):
