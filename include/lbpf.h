@@ -208,6 +208,26 @@ int lbpf_read_populations(lbpf_ctx* ctx, int domain, int which, void* out, int o
 int lbpf_measure(lbpf_ctx* ctx, int domain, int cx, int cy, int cz, double* tip6,
                  double* solid_fraction, double* conserved);
 
+/* Tip velocity of one domain (synchronises the stream): the least-squares
+ * slope, in FP64, of each tip distance of lbpf_measure (physical length:
+ * lattice units x dx) over physical time (steps x dt), over the last `window`
+ * measurements (>= 2) since the last seed; lbpf_measure records at most the
+ * last 64.  v6 receives the speeds along +x, -x, +y, -y, +z, -z (NaN where
+ * fewer than two measurements had a crossing).  The paper reports the tip
+ * velocity V_p and its dimensionless form V_p d0 / kappa, d0 = a1 W0 / lambda
+ * (Sec. 3.4); the slope fit is a reading (the paper does not say how V_p is
+ * taken).  Errors: LBPF_EINVAL (window < 2, fewer than two measurements). */
+int lbpf_tip_velocity(lbpf_ctx* ctx, int domain, int window, double* v6);
+
+/* Tip radius (lattice units) of the tip along direction dir (0..5 = +x, -x,
+ * +y, -y, +z, -z) seen from the site (cx, cy, cz): the phi = 0 crossings on
+ * the rays parallel to the axis at transverse offsets |j| <= J are fitted by
+ * x_c(j) = a + b j^2 (least squares, FP64) and rho = -1/(2b); in 3D the mean
+ * over the two transverse planes.  The paper does not define a tip radius;
+ * this is a reading.  *rho = -1 when no fit is possible.  J: 1..15 in 2D,
+ * 1..7 in 3D.  Synchronises the stream.  Errors: LBPF_EINVAL. */
+int lbpf_tip_radius(lbpf_ctx* ctx, int domain, int cx, int cy, int cz, int dir, int J, double* rho);
+
 typedef enum {
     LBPF_Q_SITES = 0,          /* total sites over all domains                       */
     LBPF_Q_STEPS = 1,          /* steps done since the last seed / write_fields      */

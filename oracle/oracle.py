@@ -239,3 +239,62 @@ class Oracle:
         cs = C.c_double()
         lib().orc_measure(self._h, cx, cy, cz, _dp(tip), C.byref(sf), C.byref(cs))
         return tip, sf.value, cs.value
+
+
+# ---------------------------------------------------------------------------
+# Tip kinetics.  The paper defines the tip velocity V_p and its dimensionless
+# form V_p d0 / kappa (Sec. 3.4) but neither the tip position nor the tip
+# radius.  Readings: the tip position is the outermost phi = 0 crossing on the
+# axis ray (orc_measure); the tip velocity is the least-squares slope of the
+# tip position over time; the tip radius is rho = -1/(2b) from the
+# least-squares fit x_c(j) = a + b j^2 of the crossings on the rays parallel to
+# the axis at transverse offsets |j| <= J (in 3D, the mean of the two
+# transverse planes).
+# ---------------------------------------------------------------------------
+
+def tip_velocity(times, positions):
+    """Least-squares slope of positions over times (a library fit as one step)."""
+    t = np.asarray(times, dtype=np.float64)
+    x = np.asarray(positions, dtype=np.float64)
+    return float(np.polyfit(t, x, 1)[0])
+
+
+def ray_crossing(phi, centre, axis, sign, offsets):
+    """Outermost phi = 0 crossing (linear interpolation) along the ray from
+    `centre` shifted by `offsets` (dict axis -> shift), in direction sign along
+    `axis`, over half the box; -1 when there is none.  phi is (nz, ny, nx)."""
+    shape = phi.shape[::-1]  # (nx, ny, nz)
+    c = list(centre)
+    for ax, sh in offsets.items():
+        c[ax] = (c[ax] + sh) % shape[ax]
+    length = shape[axis] // 2
+    best = -1.0
+    for k in range(length):
+        p0i, p1i = list(c), list(c)
+        p0i[axis] = (c[axis] + sign * k) % shape[axis]
+        p1i[axis] = (c[axis] + sign * (k + 1)) % shape[axis]
+        p0 = phi[p0i[2], p0i[1], p0i[0]]
+        p1 = phi[p1i[2], p1i[1], p1i[0]]
+        if p0 >= 0.0 and p1 < 0.0:
+            best = k + p0 / (p0 - p1)
+    return best
+
+
+def tip_radius(phi, centre, direction, J=3):
+    """Tip radius (lattice units) of the tip along direction 0..5
+    (+x, -x, +y, -y, +z, -z) from the crossings at transverse offsets |j| <= J."""
+    axis, sign = direction // 2, (1 if direction % 2 == 0 else -1)
+    dim = 3 if phi.shape[0] > 1 else 2
+    planes = [a for a in range(dim) if a != axis]
+    rhos = []
+    for tr in planes:
+        js, xs = [], []
+        for j in range(-J, J + 1):
+            x = ray_crossing(phi, centre, axis, sign, {tr: j})
+            if x >= 0:
+                js.append(j * j)
+                xs.append(x)
+        if len(js) >= 3:
+            b = np.polyfit(np.array(js, float), np.array(xs), 1)[0]
+            rhos.append(-1.0 / (2.0 * b))
+    return float(np.mean(rhos)) if rhos else -1.0

@@ -22,6 +22,8 @@ thread_local std::string t_err;
 #define LBPF_SEGMENT 0
 #endif
 
+constexpr int kHistCap = 64;
+
 // a2 of the thin-interface relations, Eq. (Kinetic-Coeff); lambda* cancels beta.
 constexpr double kA2 = 0.6267;
 
@@ -43,6 +45,9 @@ struct lbpf_ctx {
     cudaGraphExec_t graphs[8] = {};
     bool graphs_off = false;
     std::string tuned;  // how the schedule was chosen
+    // measurement history: per domain a ring of kHistCap entries (t, tip6)
+    double* d_hist = nullptr;
+    std::vector<int> hist_count, hist_last;
     cudaStream_t stream = nullptr;
     int device = 0;
     const Launchers* L = nullptr;
@@ -408,6 +413,11 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
     }
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), sizeof(double) * (3 * kReduceBlocks + 16));
     if (rc == LBPF_OK) {
+        rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_hist), sizeof(double) * 7 * kHistCap * n_domains);
+        c->hist_count.assign(n_domains, 0);
+        c->hist_last.assign(n_domains, kHistCap - 1);
+    }
+    if (rc == LBPF_OK) {
         if (cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomainDev) * n_domains, cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess)
             rc = fail(c, LBPF_ECUDA, "lbpf_create: copying the domain table failed");
@@ -476,6 +486,7 @@ extern "C" int lbpf_seed(lbpf_ctx* c, int domain, const lbpf_seed_t* seeds, int 
     CK(c->L->equilibrate(c->d_dd + domain, c->cur, c->fcur, c->acur, c->grad, 1, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->steps = 0;
+    c->hist_count[domain] = 0;
     return LBPF_OK;
 }
 
@@ -502,6 +513,7 @@ extern "C" int lbpf_write_fields(lbpf_ctx* c, int domain, const void* phi, const
     CK(c->L->equilibrate(c->d_dd + domain, c->cur, c->fcur, c->acur, c->grad, 0, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->steps = 0;
+    c->hist_count[domain] = 0;
     return LBPF_OK;
 }
 
@@ -662,6 +674,13 @@ extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, dou
     double* outp = c->red + 3 * kReduceBlocks;
     CK(launch_reduce(h.phi[c->cur], c->scratch, h.n, c->precision, c->red, outp, c->stream));
     CK(launch_tips(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, c->dim, c->precision, outp + 3, c->stream));
+    {
+        const int slot = (c->hist_last[domain] + 1) % kHistCap;
+        CK(launch_hist_append(outp + 3, (double)c->steps * c->in[domain].dt,
+                              c->d_hist + 7 * ((size_t)domain * kHistCap + slot), c->stream));
+        c->hist_last[domain] = slot;
+        if (c->hist_count[domain] < kHistCap) c->hist_count[domain] += 1;
+    }
     double hv[9];
     CK(cudaMemcpyAsync(hv, outp, sizeof(hv), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -670,6 +689,37 @@ extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, dou
     if (solid_fraction) *solid_fraction = hv[0] / (double)h.n;
     if (conserved) *conserved = hv[1];
     if (hv[2] > 0) return fail(c, LBPF_ENONFINITE, "lbpf_measure: %.0f non-finite values in phi or u", hv[2]);
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_tip_velocity(lbpf_ctx* c, int domain, int window, double* v6)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    if (!v6 || window < 2) return fail(c, LBPF_EINVAL, "lbpf_tip_velocity: need v6 and window >= 2");
+    if (c->hist_count[domain] < 2)
+        return fail(c, LBPF_EINVAL, "lbpf_tip_velocity: fewer than two measurements since the last seed");
+    double* out = c->red + 3 * kReduceBlocks + 9;
+    CK(launch_tip_velocity(c->d_hist + 7 * (size_t)domain * kHistCap, kHistCap, c->hist_last[domain],
+                           c->hist_count[domain], window, c->in[domain].dx, out, c->stream));
+    CK(cudaMemcpyAsync(v6, out, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBPF_OK;
+}
+
+extern "C" int lbpf_tip_radius(lbpf_ctx* c, int domain, int cx, int cy, int cz, int dir, int J, double* rho)
+{
+    int rc = check_ctx(c, domain);
+    if (rc) return rc;
+    const DomainDev& h = c->dd[domain];
+    if (!rho || dir < 0 || dir >= 2 * c->dim || J < 1 || (2 * J + 1) * (c->dim - 1) > 32)
+        return fail(c, LBPF_EINVAL, "lbpf_tip_radius: bad direction or J (1..15 in 2D, 1..7 in 3D)");
+    if (cx < 0 || cx >= h.nx || cy < 0 || cy >= h.ny || cz < 0 || cz >= h.nz)
+        return fail(c, LBPF_EINVAL, "lbpf_tip_radius: centre outside the domain");
+    double* out = c->red + 3 * kReduceBlocks + 15;
+    CK(launch_tip_radius(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, dir, J, c->dim, c->precision, out, c->stream));
+    CK(cudaMemcpyAsync(rho, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return LBPF_OK;
 }
 

@@ -212,3 +212,145 @@ cudaError_t launch_fill_i8(int8_t* out, int8_t v, long long n, cudaStream_t s)
 }
 
 }  // namespace lbpf
+
+namespace lbpf {
+
+// Append (time, tip6) to a domain's measurement history slot.
+__global__ void hist_append_kernel(const double* tips6, double t, double* slot)
+{
+    if (threadIdx.x == 0) slot[0] = t;
+    if (threadIdx.x < 6) slot[1 + threadIdx.x] = tips6[threadIdx.x];
+}
+
+cudaError_t launch_hist_append(const double* tips6, double t, double* slot, cudaStream_t s)
+{
+    hist_append_kernel<<<1, 32, 0, s>>>(tips6, t, slot);
+    return cudaGetLastError();
+}
+
+// Least-squares slope (FP64) of each tip distance over time, over the last
+// `window` entries of a ring of `cap` entries ending at `last`; entries with
+// no crossing (negative) are skipped.  out[d] = slope * dx (physical speed), or
+// NaN when fewer than two valid entries remain.
+__global__ void tip_velocity_kernel(const double* hist, int cap, int last, int count, int window, double dx,
+                                    double* out)
+{
+    const int d = threadIdx.x;
+    if (d >= 6) return;
+    const int m = window < count ? window : count;
+    double st = 0, sx = 0;
+    int k = 0;
+    for (int i = 0; i < m; ++i) {
+        const double* e = hist + 7 * (size_t)((last - i + cap) % cap);
+        if (e[1 + d] < 0) continue;
+        st += e[0];
+        sx += e[1 + d];
+        ++k;
+    }
+    if (k < 2) {
+        out[d] = nan("");
+        return;
+    }
+    const double tm = st / k, xm = sx / k;
+    double num = 0, den = 0;
+    for (int i = 0; i < m; ++i) {
+        const double* e = hist + 7 * (size_t)((last - i + cap) % cap);
+        if (e[1 + d] < 0) continue;
+        num += (e[0] - tm) * (e[1 + d] - xm);
+        den += (e[0] - tm) * (e[0] - tm);
+    }
+    out[d] = den > 0 ? num / den * dx : nan("");
+}
+
+cudaError_t launch_tip_velocity(const double* hist, int cap, int last, int count, int window, double dx, double* out,
+                                cudaStream_t s)
+{
+    tip_velocity_kernel<<<1, 32, 0, s>>>(hist, cap, last, count, window, dx, out);
+    return cudaGetLastError();
+}
+
+// Tip radius: warp r scans the ray parallel to the tip axis at transverse
+// offset j (ray r = plane * (2J+1) + j + J) for its outermost phi = 0
+// crossing; thread 0 then fits x_c(j) = a + b j^2 per transverse plane in FP64
+// and returns the mean of -1/(2b) over the planes (-1 when no fit).
+template <class R>
+__global__ void tip_radius_kernel(const R* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir,
+                                  int J, int dim, double* out)
+{
+    __shared__ double xc[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int axis = dir >> 1, sign = (dir & 1) ? -1 : 1;
+    const int nrow = 2 * J + 1;
+    const int nplanes = dim - 1;
+    const int nn[3] = {nx, ny, nz};
+    if (w < nrow * nplanes) {
+        const int plane = w / nrow, j = w % nrow - J;
+        int tr = -1, cnt = 0;
+        for (int a = 0; a < dim; ++a)
+            if (a != axis) {
+                if (cnt == plane) tr = a;
+                ++cnt;
+            }
+        int c[3] = {cx, cy, cz};
+        c[tr] = ((c[tr] + j) % nn[tr] + nn[tr]) % nn[tr];
+        const int len = nn[axis] / 2;
+        auto at = [&](int k) -> double {
+            int p[3] = {c[0], c[1], c[2]};
+            p[axis] = ((c[axis] + sign * k) % nn[axis] + nn[axis]) % nn[axis];
+            return (double)phi[((long long)p[2] * ny + p[1]) * nx + p[0]];
+        };
+        int best = -1;
+        for (int k = l; k < len; k += 32)
+            if (at(k) >= 0.0 && at(k + 1) < 0.0) best = k;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, o));
+        if (l == 0) {
+            if (best < 0) {
+                xc[w] = -1.0;
+            } else {
+                const double p0 = at(best), p1 = at(best + 1);
+                xc[w] = best + p0 / (p0 - p1);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        int nfit = 0;
+        for (int plane = 0; plane < nplanes; ++plane) {
+            double s1 = 0, sj = 0, sx = 0, sjj = 0, sjx = 0;
+            for (int j = -J; j <= J; ++j) {
+                const double x = xc[plane * nrow + j + J];
+                if (x < 0) continue;
+                const double q = (double)j * j;
+                s1 += 1;
+                sj += q;
+                sx += x;
+                sjj += q * q;
+                sjx += q * x;
+            }
+            const double den = s1 * sjj - sj * sj;
+            if (s1 >= 3 && den > 0) {
+                const double b = (s1 * sjx - sj * sx) / den;
+                sum += -1.0 / (2.0 * b);
+                ++nfit;
+            }
+        }
+        out[0] = nfit ? sum / nfit : -1.0;
+    }
+}
+
+cudaError_t launch_tip_radius(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir, int J, int dim,
+                              int precision, double* out, cudaStream_t s)
+{
+    const int threads = 32 * (2 * J + 1) * (dim - 1);
+    if (precision == LBPF_FP64)
+        tip_radius_kernel<double><<<1, threads, 0, s>>>(static_cast<const double*>(phi), nx, ny, nz, cx, cy, cz, dir,
+                                                         J, dim, out);
+    else
+        tip_radius_kernel<float><<<1, threads, 0, s>>>(static_cast<const float*>(phi), nx, ny, nz, cx, cy, cz, dir, J,
+                                                        dim, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbpf

@@ -332,6 +332,14 @@ cudaError_t launch_reduce(const void* phi, const void* u, long long n, int preci
 // Tip crossings along +-x, +-y, +-z from (cx, cy, cz); out[6].
 cudaError_t launch_tips(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dim, int precision,
                         double* out, cudaStream_t s);
+// Measurement history (time, tip6) per domain and the FP64 tip fits.
+cudaError_t launch_hist_append(const double* tips6, double t, double* slot, cudaStream_t s);
+cudaError_t launch_tip_velocity(const double* hist, int cap, int last, int count, int window, double dx, double* out,
+                                cudaStream_t s);
+// Tip radius of the tip along dir (0..5) from rays at transverse offsets
+// |j| <= J (J <= 7 in 3D, <= 15 in 2D); out[0].
+cudaError_t launch_tip_radius(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir, int J, int dim,
+                              int precision, double* out, cudaStream_t s);
 // int8 <-> int32 index copies.
 cudaError_t launch_index_to_i32(const int8_t* in, int* out, long long n, cudaStream_t s);
 cudaError_t launch_index_from_i32(const int* in, int8_t* out, long long n, int n_crystals, cudaStream_t s);

@@ -27,7 +27,7 @@ LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
 LBPF_MAX_CRYSTALS = 16
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
-            "lbpf_field_sums_static", "lbpf_set_schedule"]
+            "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius"]
 
 
 class lbpf_crystal(C.Structure):
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH):
     lib.lbpf_last_error.restype = C.c_char_p
     lib.lbpf_field_sums_static.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp]
     lib.lbpf_set_schedule.argtypes = [vp, C.c_int, C.c_int]
+    lib.lbpf_tip_velocity.argtypes = [vp, C.c_int, C.c_int, d]
+    lib.lbpf_tip_radius.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, d]
     for name in EXPORTED:
         lib[name].restype = lib[name].restype if name == "lbpf_last_error" else C.c_int
     _lib = lib
@@ -174,6 +176,18 @@ def lbpf_measure(ctx, domain, cx, cy, cz=0):
     return np.array(tip[:]), sf.value, cs.value
 
 
+def lbpf_tip_velocity(ctx, domain, window=10):
+    v = (C.c_double * 6)()
+    _check(load().lbpf_tip_velocity(ctx, domain, window, v), ctx)
+    return np.array(v[:])
+
+
+def lbpf_tip_radius(ctx, domain, cx, cy, cz, direction, J=3):
+    r = C.c_double()
+    _check(load().lbpf_tip_radius(ctx, domain, cx, cy, cz, direction, J, C.byref(r)), ctx)
+    return r.value
+
+
 def lbpf_set_schedule(ctx, tile_rows, segment):
     _check(load().lbpf_set_schedule(ctx, tile_rows, segment), ctx)
 
@@ -257,6 +271,12 @@ class Solver:
 
     def query(self, what):
         return lbpf_query(self.ctx, what)
+
+    def tip_velocity(self, window=10, domain=0):
+        return lbpf_tip_velocity(self.ctx, domain, window)
+
+    def tip_radius(self, cx, cy, cz, direction, J=3, domain=0):
+        return lbpf_tip_radius(self.ctx, domain, cx, cy, cz, direction, J)
 
     def close(self):
         if self.ctx:

@@ -299,3 +299,48 @@ def test_full_size_invariants(L):
     assert maxabs(core, core[::-1]) < 1e-4
     assert maxabs(core, core.transpose(1, 0, 2)) < 1e-4
     assert maxabs(core, core.transpose(2, 1, 0)) < 1e-4
+
+
+def test_tip_velocity_and_radius_match_oracle(L, O):
+    """Tip velocity (FP64 slope on the GPU over the measurement history) and
+    tip radius (parabola fit of crossings) against the oracle's readings on
+    the oracle's own run of the 2D configuration."""
+    w = W.c1(128)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 0, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"])
+    dt, dx = w["params"]["dt"], w["params"]["dx"]
+    times, tips = [], []
+    for k in range(10):
+        o.step(100)
+        s.step(100)
+        s.measure(*w["centre"])
+        tips.append(o.measure(*w["centre"])[0])
+        times.append((k + 1) * 100 * dt)
+    v = s.tip_velocity(window=8)
+    tips = np.array(tips)
+    for d in range(4):
+        ov = O.tip_velocity(times[-8:], tips[-8:, d] * dx)
+        assert abs(v[d] - ov) <= 1e-9 * abs(ov), (d, v[d], ov)
+    assert v[0] > 0 and np.isnan(v[4])
+    phi_o = o.fields()[0]
+    for d in range(4):
+        r = s.tip_radius(*w["centre"], d, J=3)
+        ro = O.tip_radius(phi_o, w["centre"], d, J=3)
+        assert abs(r - ro) <= 1e-8 * abs(ro), (d, r, ro)
+    assert 1.0 < ro < 100.0
+    with pytest.raises(L.LbpfError):
+        s.tip_radius(*w["centre"], 0, J=40)
+
+
+def test_tip_radius_3d_matches_oracle(L, O):
+    w = W.c2(48)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    o.step(300)
+    s.step(300)
+    for d in range(6):
+        r = s.tip_radius(*w["centre"], d, J=3)
+        ro = O.tip_radius(o.fields()[0], w["centre"], d, J=3)
+        assert abs(r - ro) <= 1e-8 * abs(ro), (d, r, ro)
