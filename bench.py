@@ -221,6 +221,74 @@ def run_reference(args):
     return 0
 
 
+def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
+    """Surrogate + LB vs plain LB on one 2D domain of the batched
+    configuration's distributions: same final time, tip velocity from the
+    last LB measurements, wall-clock time to solution."""
+    import torch
+    from paper_1606_09432_gb300 import build as B
+    B.build()
+    from paper_1606_09432_gb300 import lbpf as L
+    from paper_1606_09432_gb300 import surrogate as S
+    from paper_1606_09432_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    X, Y = S.generate_pairs(W.surrogate_draws(16, size=train_size, seed=7), 2000, 50, torch)
+    net = L.Net(train_size, train_size, batch=8, seed=1)
+    hist = S.train(net, X, Y, 1500, lr=1e-3, torch=torch)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    d = W.surrogate_draws(1, size=size, seed=99)[0]
+    d["seeds"] = [(size / 2, size / 2, 0.0, 10.0, 0)]
+    d["crystals"] = d["crystals"][:1]
+    centre = (size // 2, size // 2, 0)
+    inf = L.Net(size, size, batch=1, seed=0)
+    inf.set_params(net.params())
+
+    def solver():
+        s = L.Solver([S._domain(d)], L.LBPF_D2Q9_D2Q5, L.LBPF_GRAD_DD, L.LBPF_FP32)
+        s.seed(d["seeds"])
+        return s
+
+    def tipv(s, window=200):
+        a = np.max(s.measure(*centre)[0][:4])
+        s.step(window)
+        b = np.max(s.measure(*centre)[0][:4])
+        return (b - a) / window
+
+    sp = solver()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sp.step(steps_total)
+    sp.measure(*centre)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t1
+    sc = solver()
+    ctl = S.Controller(sc, inf, d, centre, torch, K=50, M=4, kv=20)
+    st = ctl.run(steps_total)
+    v_plain, v_sur = tipv(sp), tipv(sc)
+    xx = torch.zeros((1, size, size, 5), device="cuda")
+    yy = torch.empty((1, size, size, 2), device="cuda")
+    inf.forward(xx, yy)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for _ in range(10):
+        inf.forward(xx, yy)
+    torch.cuda.synchronize()
+    t_net = (time.perf_counter() - t2) / 10
+    line = {"metric": "surrogate + LB vs plain LB time to solution", "value": round(t_plain / st.seconds, 4),
+            "unit": "x (plain LB time / surrogate+LB time)", "higher_is_better": True, "n_gpus": 1,
+            "config": {"workload": f"2D {size}^2 periodic, D2Q9/D2Q5 FP32, one seed R=10, {steps_total} steps, "
+                                   f"K=50, M=4, k_v=20, network trained on 16 draws at {train_size}^2"},
+            "plain_lb_s": round(t_plain, 4), "surrogate_lb_s": round(st.seconds, 4),
+            "jumps_accepted": st.jumps_accepted, "blocks_rejected": st.blocks_rejected,
+            "tip_velocity_rel_err": round(abs(v_sur - v_plain) / abs(v_plain), 4) if v_plain else None,
+            "net_forward_ms": round(t_net * 1e3, 3), "train_s": round(t_train, 2),
+            "train_loss_last": float(np.mean(hist[-50:])), "predict_zero_loss": float((Y ** 2).mean().item())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,11 +299,15 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="override the cube edge of the workload (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="time-to-solution of surrogate + LB vs plain LB (trains a network first)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

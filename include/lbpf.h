@@ -273,6 +273,55 @@ int lbpf_query(const lbpf_ctx* ctx, int what, double* value);
 int lbpf_field_sums_static(const void* phi, const void* u, long long n, int precision, double* out,
                            void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (not in the paper): a 2D U-Net that predicts the change
+ * of phi and u over a jump of K lattice Boltzmann steps, used by a controller
+ * that alternates network jumps with plain LB validation and falls back to LB.
+ * Architecture: three levels of two periodic 3x3 convolutions + ReLU (16, 32,
+ * 64 channels), 2x2 average pooling, nearest 2x upsampling with skip
+ * concatenation, 1x1 head to 2 channels.  Input per site (NHWC, FP32):
+ * (phi, u, cos 4 theta, sin 4 theta, eps); output (d phi, d u), the phi
+ * channel multiplied by (1 - phi^2) so that the bulk phases stay fixed.  3x3
+ * convolutions run on the tensor cores with BF16 operands (weights and
+ * staged activations) and FP32 accumulation; everything else in FP32.
+ * Parameters: one flat FP32 vector (per 3x3 layer weights [tap][cout][cin]
+ * then biases, then the head's [2][16] weights and 2 biases).
+ * All device pointers below are device memory of the current GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct lbpf_net lbpf_net;
+
+/* Network for batches of `batch` images of H x W sites (H, W multiples of
+ * 32), He-uniform weights from `seed`.  Errors: LBPF_EINVAL, LBPF_ENOMEM. */
+int lbpf_net_create(int H, int W, int batch, unsigned long long seed, void* stream, lbpf_net** out);
+int lbpf_net_destroy(lbpf_net* net);
+const char* lbpf_net_last_error(const lbpf_net* net);
+int lbpf_net_num_params(const lbpf_net* net, long long* n);
+/* Copy the parameters (which = 0) or the last gradients (which = 1) to host. */
+int lbpf_net_get_params(lbpf_net* net, float* host, int which);
+int lbpf_net_set_params(lbpf_net* net, const float* host);
+/* y (N, H, W, 2) = network(x (N, H, W, 5)); y may be NULL (output kept). */
+int lbpf_net_forward(lbpf_net* net, const float* x, float* y);
+/* Parameter gradients of sum(out * dy) after a forward pass (read them with
+ * lbpf_net_get_params(which = 1)). */
+int lbpf_net_backward(lbpf_net* net, const float* dy);
+/* One Adam step (beta 0.9, 0.999) on the mean squared error to `target`
+ * (N, H, W, 2); *loss (may be NULL) receives the loss before the step. */
+int lbpf_net_train_step(lbpf_net* net, const float* x, const float* target, float lr, double* loss);
+/* Network input from fields: x[p] = (phi, u, cos 4 theta, sin 4 theta, eps)
+ * of the crystal I = index[p] (1 everywhere when index is NULL; zeros for
+ * I = 0 or I > n_crystals), crystal_tab[2 (I-1)] = eps, [2 (I-1) + 1] = theta. */
+int lbpf_net_assemble(const float* phi, const float* u, const int* index, const float* crystal_tab,
+                      int n_crystals, float* x, long long sites, void* stream);
+/* phi += y[.][0], u += y[.][1] (a network jump). */
+int lbpf_net_apply(const float* y, float* phi, float* u, long long sites, void* stream);
+/* y = (phi1 - phi0, u1 - u0) per site: the training target of a jump. */
+int lbpf_net_delta(const float* phi0, const float* u0, const float* phi1, const float* u1, float* y,
+                   long long sites, void* stream);
+/* *count (device unsigned int) = number of sites with phi outside [lo, hi]
+ * or not finite (the controller's fall-back test). */
+int lbpf_net_range_check(const float* phi, long long sites, float lo, float hi, unsigned int* count,
+                         void* stream);
+
 /* Release every resource of the context (NULL is accepted).  Synchronises
  * the stream first. */
 int lbpf_destroy(lbpf_ctx* ctx);

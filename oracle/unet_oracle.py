@@ -1,0 +1,184 @@
+"""FP64 NumPy oracle of the learned surrogate's U-Net (test infrastructure).
+
+Same architecture and flat parameter layout as the CUDA network
+(include/lbpf.h, "Learned surrogate"): three levels of two periodic 3x3
+convolutions + ReLU (16, 32, 64 channels), 2x2 average pooling, nearest 2x
+upsampling with skip concatenation, 1x1 head to 2 channels whose phi channel
+is gated by (1 - phi^2); input (N, H, W, 5) zero-padded to 16 channels.  The
+backward pass is written out layer by layer (plain chain rule).  With
+emulate=True the operands of every 3x3 convolution
+(weights, and the activations or gradients it reads) are rounded to BF16
+first, as the tensor-core kernels do; accumulation stays FP64.
+
+The surrogate is not part of the paper; nothing here is pinned by the paper.
+The pins are mathematical: a brute-force periodic convolution, adjointness of
+pooling and upsampling, and finite differences of the loss.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LAYERS = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
+N_IN, N_IN_PAD, N_OUT = 5, 16, 2
+
+
+def n_params():
+    return sum(9 * ci * co + co for ci, co in LAYERS) + N_OUT * 16 + N_OUT
+
+
+def unpack(p):
+    """Flat vector -> list of (W[tap][co][ci], b[co]) for the 3x3 layers, and
+    the head (W[co][ci], b[co])."""
+    p = np.asarray(p, dtype=np.float64)
+    out, k = [], 0
+    for ci, co in LAYERS:
+        w = p[k:k + 9 * ci * co].reshape(9, co, ci)
+        k += 9 * ci * co
+        b = p[k:k + co]
+        k += co
+        out.append((w, b))
+    hw = p[k:k + N_OUT * 16].reshape(N_OUT, 16)
+    k += N_OUT * 16
+    hb = p[k:k + N_OUT]
+    return out, (hw, hb)
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    r = ((bits + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def shift(x, dy, dx):
+    """x[n, (y + dy) mod H, (x + dx) mod W, c]."""
+    return np.roll(np.roll(x, -dy, axis=1), -dx, axis=2)
+
+
+def conv3x3(x, w, b=None, emulate=False):
+    """Periodic 3x3 convolution y[p][co] = b[co] + sum_tap sum_ci w[tap][co][ci] x[p + tap][ci]."""
+    if emulate:
+        x, w = bf16(x), bf16(w)
+    y = np.zeros(x.shape[:3] + (w.shape[1],))
+    for tap in range(9):
+        dy, dx = tap // 3 - 1, tap % 3 - 1
+        y += shift(x, dy, dx) @ w[tap].T
+    if b is not None:
+        y += b
+    return y
+
+
+def conv3x3_dgrad(dy, w, emulate=False):
+    """Adjoint of conv3x3 in its input: dx[p][ci] = sum_tap sum_co w[tap][co][ci] dy[p - tap][co]."""
+    if emulate:
+        dy, w = bf16(dy), bf16(w)
+    dx = np.zeros(dy.shape[:3] + (w.shape[2],))
+    for tap in range(9):
+        ddy, ddx = tap // 3 - 1, tap % 3 - 1
+        dx += shift(dy, -ddy, -ddx) @ w[tap]
+    return dx
+
+
+def conv3x3_wgrad(x, dy):
+    """dw[tap][co][ci] = sum_p dy[p][co] x[p + tap][ci] (FP64)."""
+    co, ci = dy.shape[-1], x.shape[-1]
+    dw = np.zeros((9, co, ci))
+    for tap in range(9):
+        ddy, ddx = tap // 3 - 1, tap % 3 - 1
+        dw[tap] = np.einsum("nhwo,nhwi->oi", dy, shift(x, ddy, ddx))
+    return dw
+
+
+def pool(x):
+    n, h, w, c = x.shape
+    return x.reshape(n, h // 2, 2, w // 2, 2, c).mean(axis=(2, 4))
+
+
+def pool_bwd(dy):
+    return np.repeat(np.repeat(dy, 2, axis=1), 2, axis=2) * 0.25
+
+
+def up(x):
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def up_bwd(dy):
+    n, h, w, c = dy.shape
+    return dy.reshape(n, h // 2, 2, w // 2, 2, c).sum(axis=(2, 4))
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def forward(p, x, emulate=False):
+    """Returns (out, cache)."""
+    L, (hw, hb) = unpack(p)
+    xin = np.concatenate([x, np.zeros(x.shape[:3] + (N_IN_PAD - x.shape[3],))], axis=3)
+    c = {"xin": xin}
+    cv = lambda k, a: relu(conv3x3(a, L[k][0], L[k][1], emulate))
+    c["a1a"] = cv(0, xin)
+    c["a1"] = cv(1, c["a1a"])
+    c["p1"] = pool(c["a1"])
+    c["a2a"] = cv(2, c["p1"])
+    c["a2"] = cv(3, c["a2a"])
+    c["p2"] = pool(c["a2"])
+    c["a3a"] = cv(4, c["p2"])
+    c["a3"] = cv(5, c["a3a"])
+    c["u2"] = np.concatenate([up(c["a3"]), c["a2"]], axis=3)
+    c["d2a"] = cv(6, c["u2"])
+    c["d2"] = cv(7, c["d2a"])
+    c["u1"] = np.concatenate([up(c["d2"]), c["a1"]], axis=3)
+    c["d1a"] = cv(8, c["u1"])
+    c["d1"] = cv(9, c["d1a"])
+    out = c["d1"] @ hw.T + hb
+    out[..., 0] *= 1.0 - xin[..., 0] ** 2  # interface gate of the phi output
+    return out, c
+
+
+def backward(p, c, dout, emulate=False):
+    """Gradient of sum(out * dout) with respect to the flat parameter vector."""
+    L, (hw, hb) = unpack(p)
+    grads = [None] * len(LAYERS)
+    dout = dout.copy()
+    dout[..., 0] *= 1.0 - c["xin"][..., 0] ** 2
+
+    def cvb(k, a_in, y, dy, need_dx=True):
+        dy = dy * (y > 0)
+        grads[k] = (conv3x3_wgrad(a_in, dy), dy.sum(axis=(0, 1, 2)))
+        return conv3x3_dgrad(dy, L[k][0], emulate) if need_dx else None
+
+    ghw = np.einsum("nhwo,nhwi->oi", dout, c["d1"])
+    ghb = dout.sum(axis=(0, 1, 2))
+    g = dout @ hw
+    g = cvb(9, c["d1a"], c["d1"], g)
+    g = cvb(8, c["u1"], c["d1a"], g)
+    g_d2, g_a1 = up_bwd(g[..., :32]), g[..., 32:]
+    g = cvb(7, c["d2a"], c["d2"], g_d2)
+    g = cvb(6, c["u2"], c["d2a"], g)
+    g_a3, g_a2 = up_bwd(g[..., :64]), g[..., 64:]
+    g = cvb(5, c["a3a"], c["a3"], g_a3)
+    g = cvb(4, c["p2"], c["a3a"], g)
+    g_a2 = g_a2 + pool_bwd(g)
+    g = cvb(3, c["a2a"], c["a2"], g_a2)
+    g = cvb(2, c["p1"], c["a2a"], g)
+    g_a1 = g_a1 + pool_bwd(g)
+    g = cvb(1, c["a1a"], c["a1"], g_a1)
+    cvb(0, c["xin"], c["a1a"], g, need_dx=False)
+    flat = []
+    for dw, db in grads:
+        flat += [dw.ravel(), db]
+    flat += [ghw.ravel(), ghb]
+    return np.concatenate(flat)
+
+
+def init_params(seed, scale_head=1e-2):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in LAYERS:
+        a = np.sqrt(6.0 / (9 * ci))
+        parts += [rng.uniform(-a, a, 9 * co * ci), np.zeros(co)]
+    parts += [rng.uniform(-scale_head, scale_head, N_OUT * 16), np.zeros(N_OUT)]
+    return np.concatenate(parts)

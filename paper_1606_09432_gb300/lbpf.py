@@ -27,7 +27,11 @@ LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
 LBPF_MAX_CRYSTALS = 16
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
-            "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius"]
+            "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius",
+            "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
+            "lbpf_net_get_params", "lbpf_net_set_params", "lbpf_net_forward", "lbpf_net_backward",
+            "lbpf_net_train_step", "lbpf_net_assemble", "lbpf_net_apply", "lbpf_net_delta",
+            "lbpf_net_range_check"]
 
 
 class lbpf_crystal(C.Structure):
@@ -79,8 +83,23 @@ def load(path: str = LIB_PATH):
     lib.lbpf_set_schedule.argtypes = [vp, C.c_int, C.c_int]
     lib.lbpf_tip_velocity.argtypes = [vp, C.c_int, C.c_int, d]
     lib.lbpf_tip_radius.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, d]
+    lib.lbpf_net_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp, C.POINTER(vp)]
+    lib.lbpf_net_destroy.argtypes = [vp]
+    lib.lbpf_net_last_error.argtypes = [vp]
+    lib.lbpf_net_num_params.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.lbpf_net_get_params.argtypes = [vp, vp, C.c_int]
+    lib.lbpf_net_set_params.argtypes = [vp, vp]
+    lib.lbpf_net_forward.argtypes = [vp, vp, vp]
+    lib.lbpf_net_backward.argtypes = [vp, vp]
+    lib.lbpf_net_train_step.argtypes = [vp, vp, vp, C.c_float, d]
+    lib.lbpf_net_assemble.argtypes = [vp, vp, vp, vp, C.c_int, vp, C.c_longlong, vp]
+    lib.lbpf_net_apply.argtypes = [vp, vp, vp, C.c_longlong, vp]
+    lib.lbpf_net_delta.argtypes = [vp, vp, vp, vp, vp, C.c_longlong, vp]
+    lib.lbpf_net_range_check.argtypes = [vp, C.c_longlong, C.c_float, C.c_float, vp, vp]
     for name in EXPORTED:
-        lib[name].restype = lib[name].restype if name == "lbpf_last_error" else C.c_int
+        lib[name].restype = C.c_int
+    lib.lbpf_last_error.restype = C.c_char_p
+    lib.lbpf_net_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -288,3 +307,96 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate network (include/lbpf.h, "Learned surrogate").
+# ---------------------------------------------------------------------------
+
+def _dptr(t):
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Net:
+    """The surrogate U-Net for batches of `batch` H x W images (NHWC float32
+    CUDA tensors: input (N, H, W, 5), output (N, H, W, 2))."""
+
+    def __init__(self, H, W, batch=1, seed=0, stream=None):
+        self.H, self.W, self.batch = H, W, batch
+        self.stream = stream
+        self.h = C.c_void_p()
+        rc = load().lbpf_net_create(H, W, batch, seed, C.c_void_p(stream) if stream else None, C.byref(self.h))
+        if rc != LBPF_OK:
+            raise LbpfError(rc, load().lbpf_net_last_error(None).decode())
+        n = C.c_longlong()
+        load().lbpf_net_num_params(self.h, C.byref(n))
+        self.n_params = n.value
+
+    def _chk(self, rc):
+        if rc != LBPF_OK:
+            raise LbpfError(rc, load().lbpf_net_last_error(self.h).decode())
+
+    def params(self, which=0):
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._chk(load().lbpf_net_get_params(self.h, C.c_void_p(out.ctypes.data), which))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._chk(load().lbpf_net_set_params(self.h, C.c_void_p(p.ctypes.data)))
+
+    def forward(self, x, y=None):
+        self._chk(load().lbpf_net_forward(self.h, _dptr(x), _dptr(y) if y is not None else None))
+        return y
+
+    def backward(self, dy):
+        self._chk(load().lbpf_net_backward(self.h, _dptr(dy)))
+        return self.params(which=1)
+
+    def train_step(self, x, target, lr):
+        loss = C.c_double()
+        self._chk(load().lbpf_net_train_step(self.h, _dptr(x), _dptr(target), lr, C.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.h:
+            load().lbpf_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_assemble(phi, u, index, crystal_tab, x, stream=None):
+    """x (P, 5) from phi, u (P,), index (P,) int32 or None and the crystal table (nc, 2) = (eps, theta)."""
+    tab = crystal_tab.reshape(-1)
+    rc = load().lbpf_net_assemble(_dptr(phi), _dptr(u), _dptr(index) if index is not None else None, _dptr(tab),
+                                  tab.numel() // 2, _dptr(x), phi.numel(), C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_net_assemble failed")
+
+
+def net_apply(y, phi, u, stream=None):
+    rc = load().lbpf_net_apply(_dptr(y), _dptr(phi), _dptr(u), phi.numel(), C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_net_apply failed")
+
+
+def net_delta(phi0, u0, phi1, u1, y, stream=None):
+    rc = load().lbpf_net_delta(_dptr(phi0), _dptr(u0), _dptr(phi1), _dptr(u1), _dptr(y), phi0.numel(),
+                               C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_net_delta failed")
+
+
+def net_range_check(phi, lo, hi, count, stream=None):
+    """count: a 1-element int32 CUDA tensor; returns nothing (read count after synchronising)."""
+    rc = load().lbpf_net_range_check(_dptr(phi), phi.numel(), lo, hi, _dptr(count),
+                                     C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_net_range_check failed")

@@ -90,3 +90,27 @@ def c4(n_domains=64, seed=1606094320, lmin=128, lmax=1024, max_seeds=12):
                 seeds.append((x, y, 0.0, r, len(seeds)))
         out.append(dict(shape=(1, L, L), params=dict(C4_PARAMS, delta=delta), crystals=crystals, seeds=seeds))
     return out
+
+
+def surrogate_draws(n, size=128, seed=20260101, max_seeds=2):
+    """Random single-domain 2D draws for the surrogate's training data, with
+    the batched configuration's distributions (parameter set of Sec. 4.3):
+    1..max_seeds seeds of radius U[4, 10], angle-form crystals q = 4 with
+    theta ~ U[0, pi/2), eps ~ U[0.01, 0.07], Delta ~ U[0.2, 0.6]."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        ns = rng.randint(1, max_seeds)
+        delta = rng.uniform(0.2, 0.6)
+        seeds, crystals = [], []
+        tries = 0
+        while len(seeds) < ns and tries < 1000:
+            tries += 1
+            r = rng.uniform(4.0, 10.0)
+            x, y = rng.uniform(0, size), rng.uniform(0, size)
+            if all(math.hypot((x - sx + size / 2) % size - size / 2, (y - sy + size / 2) % size - size / 2) >= r + sr + 4.0
+                   for (sx, sy, _, sr, _) in seeds):
+                crystals.append(dict(kind=1, eps=rng.uniform(0.01, 0.07), q=4, phi0=rng.uniform(0, math.pi / 2)))
+                seeds.append((x, y, 0.0, r, len(seeds)))
+        out.append(dict(shape=(1, size, size), params=dict(C4_PARAMS, delta=delta), crystals=crystals, seeds=seeds))
+    return out

@@ -1,0 +1,100 @@
+"""GPU tests of the learned surrogate: the CUDA U-Net (tensor-core 3x3
+convolutions with BF16 operands, FP32 accumulation) against the FP64 oracle
+that emulates the BF16 operand rounding; training on LB trajectories; the
+controller's fall-back to LB."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from oracle import unet_oracle as U
+    from paper_1606_09432_gb300 import build as B
+    from paper_1606_09432_gb300 import lbpf as L
+    from paper_1606_09432_gb300 import surrogate as S
+    from paper_1606_09432_gb300 import workloads as W
+    B.build()
+    return torch, U, L, S, W
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_forward_backward_match_oracle(env):
+    torch, U, L, S, W = env
+    net = L.Net(32, 64, batch=2, seed=5)
+    p = net.params().astype(np.float64)
+    assert p.size == U.n_params()
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 32, 64, 5)).astype(np.float32)
+    x[..., 0] = np.tanh(x[..., 0])
+    y = torch.empty((2, 32, 64, 2), device="cuda")
+    net.forward(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    yo, cache = U.forward(p, x.astype(np.float64), emulate=True)
+    assert relerr(y.cpu().numpy(), yo) < 5e-3
+    dy = rng.standard_normal((2, 32, 64, 2)).astype(np.float32)
+    g = net.backward(torch.from_numpy(dy).cuda())
+    go = U.backward(p, cache, dy.astype(np.float64), emulate=True)
+    # BF16 operands: an activation on the other side of a BF16 rounding
+    # boundary or of a ReLU kink changes single gradient terms
+    assert relerr(g, go) < 2e-2
+    off = 0
+    for ci, co in U.LAYERS:
+        n = 9 * ci * co
+        assert relerr(g[off:off + n], go[off:off + n]) < 6e-2
+        off += n + co
+
+
+def test_training_learns_lb_increments(env):
+    torch, U, L, S, W = env
+    draws = W.surrogate_draws(12, size=64, seed=11)
+    X, Y = S.generate_pairs(draws, 1000, 50, torch)
+    # pairs are ordered (time, draw): hold out the last two draws entirely
+    d = len(draws)
+    test = torch.tensor([k for k in range(X.shape[0]) if k % d >= d - 2], device="cuda")
+    train = torch.tensor([k for k in range(X.shape[0]) if k % d < d - 2], device="cuda")
+    Xtr, Ytr = X.index_select(0, train).contiguous(), Y.index_select(0, train).contiguous()
+    Xte, Yte = X.index_select(0, test).contiguous(), Y.index_select(0, test).contiguous()
+    n_test = Xte.shape[0]
+    net = L.Net(64, 64, batch=8, seed=1)
+    S.train(net, Xtr, Ytr, 1000, lr=1e-3, torch=torch)
+    ev = L.Net(64, 64, batch=n_test, seed=0)
+    ev.set_params(net.params())
+    pred = torch.empty_like(Yte)
+    ev.forward(Xte, pred)
+    torch.cuda.synchronize()
+    mse = ((pred - Yte) ** 2).mean().item()
+    base = (Yte ** 2).mean().item()  # the method without the network: no change predicted
+    print(f"held-out MSE {mse:.3e} vs {base:.3e} for predicting no change")
+    assert mse < 0.7 * base
+
+
+def test_controller_falls_back_to_lb(env):
+    """An untrained network is rejected by the LB validation; the run then
+    advances by plain LB and ends close to the plain LB run."""
+    torch, U, L, S, W = env
+    d = W.surrogate_draws(1, size=64, seed=3)[0]
+    centre = (int(d["seeds"][0][0]), int(d["seeds"][0][1]), 0)
+    net = L.Net(64, 64, batch=1, seed=9)
+
+    def solver():
+        s = L.Solver([S._domain(d)], L.LBPF_D2Q9_D2Q5, L.LBPF_GRAD_DD, L.LBPF_FP32)
+        s.seed(d["seeds"])
+        return s
+
+    ref = solver()
+    ref.step(1320)
+    run = solver()
+    c = S.Controller(run, net, d, centre, torch, K=50, M=4, kv=20)
+    st = c.run(1320)
+    assert st.steps == 1320 and st.jumps_accepted + st.blocks_rejected * 4 == 6 * 4
+    assert st.blocks_rejected == 6
+    tip_ref = np.max(ref.measure(*centre)[0][:4])
+    tip_run = np.max(run.measure(*centre)[0][:4])
+    assert abs(tip_run - tip_ref) < 0.1
