@@ -262,7 +262,7 @@ static int choose_schedule(lbpf_ctx* c)
     for (const DomainDev& d : c->dd) sites += (double)d.n;
     const char* env = getenv("LBPF_AUTOTUNE");
     const bool tune = env ? atoi(env) != 0 : sites >= 4e6;
-    int best_v = c->dim == 3 ? 0 : 1, best_seg = default_segment(c, best_v);
+    int best_v = 0, best_seg = default_segment(c, best_v);
     if (tune) {
         double best_t = 1e30;
         for (int v = 0; v < kNumTileVariants; ++v) {
