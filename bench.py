@@ -37,12 +37,15 @@ WORKLOADS = {
                        "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 2, 512),
     "c3-512-bf16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with BF16 deviation storage, "
                        "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 3, 512),
+    "c3-512-fp16dev-sr": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with FP16 deviation storage rounded "
+                          "stochastically, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 4, 512),
     "c3-512-fp32": ("3D 512^3 periodic, D3Q15/D3Q7, FP32, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 1, 512),
     "c4-batch64-fp32": ("batched 2D multi-crystal: 64 periodic domains, sides U{128..1024} (24.4 M sites), D2Q9/D2Q5, "
                         "FP32, 1-12 seeds each with its own angle-form crystal (q=4, theta, eps), Delta per domain, "
                         "one launch per step, CUDA graphs", 0, 1, 0),
 }
-DTYPE = {0: "f64", 1: "f32", 2: "f32 arithmetic, f16 storage", 3: "f32 arithmetic, bf16 storage"}
+DTYPE = {0: "f64", 1: "f32", 2: "f32 arithmetic, f16 storage", 3: "f32 arithmetic, bf16 storage",
+         4: "f32 arithmetic, f16 storage (stochastic rounding)"}
 METRIC = "fused phi+u LB step MLUPS"
 KERNEL_SOURCES = ["step_kernel.cuh", "lbpf_internal.cuh"]
 

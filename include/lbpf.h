@@ -72,12 +72,22 @@ typedef enum { LBPF_GRAD_DD = 0, LBPF_GRAD_FD = 1 } lbpf_grad;
  *                      deviations g_i - w_i phi and f_i - w_i u for i >= 1
  *                      (the rest population is rebuilt so that the sums
  *                      phi = sum g_i, u = sum f_i hold exactly).
- *   LBPF_FP32_BF16DEV: as above with BF16 deviations. */
+ *   LBPF_FP32_BF16DEV: as above with BF16 deviations.
+ *   LBPF_FP32_FP16DEV_SR: FP16 deviations rounded stochastically (up or
+ *                      down with probabilities given by the distances, so the
+ *                      rounding errors of slowly varying values do not add up
+ *                      step after step); the random bits come from a hash of
+ *                      site, population and a step counter kept on the device,
+ *                      so runs are reproducible.  About half the FP16 error of
+ *                      round-to-nearest on a growing dendrite.  (There is no
+ *                      BF16 counterpart: noise of BF16 size at the interface
+ *                      is amplified by the growth instability.) */
 typedef enum {
     LBPF_FP64 = 0,
     LBPF_FP32 = 1,
     LBPF_FP32_FP16DEV = 2,
-    LBPF_FP32_BF16DEV = 3
+    LBPF_FP32_BF16DEV = 3,
+    LBPF_FP32_FP16DEV_SR = 4
 } lbpf_precision;
 
 /* Anisotropy functions a_s(n), n = -grad(phi)/|grad(phi)|, Eq. (Def_Normal_Vector).

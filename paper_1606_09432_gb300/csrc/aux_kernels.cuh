@@ -300,6 +300,7 @@ const Launchers* launchers_for(int precision)
     case LBPF_FP32: return LauncherImpl<PL, UL, StoreF32>::get();
     case LBPF_FP32_FP16DEV: return LauncherImpl<PL, UL, StoreF16>::get();
     case LBPF_FP32_BF16DEV: return LauncherImpl<PL, UL, StoreB16>::get();
+    case LBPF_FP32_FP16DEV_SR: return LauncherImpl<PL, UL, StoreF16SR>::get();
     default: return nullptr;
     }
 }

@@ -279,7 +279,7 @@ static int choose_schedule(lbpf_ctx* c)
                 }
             }
         }
-        CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream));
+        CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 4, c->stream));
         c->tuned = "timed";
         if (FILE* f = fopen(path.c_str(), "a")) {
             fprintf(f, "%s %d %d\n", key.c_str(), best_v, best_seg);
@@ -335,7 +335,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
     c->L = L;
     c->Qg = L->Qphi;
     c->Qu = L->Qu;
-    const bool dev = precision == LBPF_FP32_FP16DEV || precision == LBPF_FP32_BF16DEV;
+    const bool dev = precision >= LBPF_FP32_FP16DEV;
     c->Sg = dev ? c->Qg - 1 : c->Qg;
     c->Su = dev ? c->Qu - 1 : c->Qu;
     c->rsize = precision == LBPF_FP64 ? 8 : 4;
@@ -403,8 +403,8 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
             if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
         }
     }
-    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 2);
-    if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
+    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 4);
+    if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 4, c->stream) != cudaSuccess)
         rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_dd), sizeof(DomainDev) * n_domains);
     if (rc == LBPF_OK) {

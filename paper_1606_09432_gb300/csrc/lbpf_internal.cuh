@@ -121,6 +121,10 @@ struct StoreF64 { using Real = double; using T = double; static constexpr bool d
 struct StoreF32 { using Real = float; using T = float; static constexpr bool dev = false; };
 struct StoreF16 { using Real = float; using T = __half; static constexpr bool dev = true; };
 struct StoreB16 { using Real = float; using T = __nv_bfloat16; static constexpr bool dev = true; };
+// as above, deviations rounded stochastically
+struct StoreF16SR : StoreF16 { static constexpr bool sr = true; };
+template <class S, class = void> struct UsesSR { static constexpr bool value = false; };
+template <class S> struct UsesSR<S, decltype(void(S::sr))> { static constexpr bool value = S::sr; };
 
 __device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -132,6 +136,50 @@ template <> __device__ __forceinline__ double from_real<double, double>(double v
 template <> __device__ __forceinline__ float from_real<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __half from_real<__half, float>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+// Stochastic rounding of 16-bit deviations: round up or down with
+// probabilities proportional to the distances, so that rounding errors of
+// slowly varying values do not add up step after step.  Random bits come from
+// a hash of (site, population, step seed) (lowbias32 finaliser, Wellons 2018),
+// so results are reproducible.
+__device__ __forceinline__ uint32_t sr_hash(uint32_t site, uint32_t seed)
+{
+    uint32_t x = site * 0x9E3779B9u ^ seed * 0xC2B2AE35u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// Bits for population `pop` from the site hash h (one multiply-xorshift).
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, uint32_t pop)
+{
+    uint32_t x = (h ^ (pop * 0x9E3779B9u)) * 0x85EBCA6Bu;
+    return x ^ (x >> 13);
+}
+
+template <class T> __device__ __forceinline__ T from_real_sr(float v, uint32_t rnd);
+// full-precision storage: nothing to round stochastically
+template <> __device__ __forceinline__ float from_real_sr<float>(float v, uint32_t) { return v; }
+template <> __device__ __forceinline__ double from_real_sr<double>(float v, uint32_t) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_real_sr<__nv_bfloat16>(float v, uint32_t rnd)
+{
+    const uint32_t b = __float_as_uint(v);
+    if (((b >> 23) & 0xFF) == 0xFF) return __float2bfloat16_rn(v);  // Inf, NaN
+    // add 16 random bits below the BF16 mantissa, then truncate
+    return __ushort_as_bfloat16((unsigned short)((b + (rnd & 0xFFFFu)) >> 16));
+}
+template <> __device__ __forceinline__ __half from_real_sr<__half>(float v, uint32_t rnd)
+{
+    const uint32_t b = __float_as_uint(v);
+    int e = (int)((b >> 23) & 0xFF) - 127;
+    if (e > 15) return __float2half_rn(v);  // beyond the FP16 range (and Inf, NaN)
+    if (e < -14) e = -14;                   // FP16 subnormal spacing 2^-24
+    const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
+    const float r = (float)(rnd >> 8) * (1.0f / 16777216.0f) - 0.5f;  // U[-1/2, 1/2)
+    return __float2half_rn(v + r * ulp);
+}
 
 // Number of stored arrays per population set.
 template <class S, int Q> struct NStored { static constexpr int value = S::dev ? Q - 1 : Q; };
@@ -174,7 +222,7 @@ struct StepArgs {
     const DomainDev* doms;
     const WorkItem* items;
     int n_items;
-    int* counters;         // two work counters, used alternately (see step_kernel)
+    int* counters;         // [0..1] work counters, [2..3] rounding seeds, used alternately
     int cur;    // g / phi / I buffer holding time n (new = cur ^ 1)
     int fcur;   // f buffer read (f^{n-1} when collide, f^n when load)
     int acur;   // aux buffer read (new = acur ^ 1)

@@ -94,7 +94,7 @@ extern "C" int lbpf_field_sums_static(const void* phi, const void* u, long long 
                                       void* stream)
 {
     if (!phi || !u || !out) return LBPF_EINVAL;
-    if (precision < LBPF_FP64 || precision > LBPF_FP32_BF16DEV) return LBPF_EINVAL;
+    if (precision < LBPF_FP64 || precision > LBPF_FP32_FP16DEV_SR) return LBPF_EINVAL;
     if (n < 1 || n > kStaticMaxSites) return LBPF_ERANGE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -136,6 +136,16 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     const int8_t* __restrict__ Ic = dm.I[args.cur];
     int8_t* __restrict__ In = dm.I[args.cur ^ 1];
 
+    constexpr bool SR = UsesSR<S>::value;
+    const uint32_t seed = SR ? (uint32_t)args.counters[2 + args.cur] : 0u;
+    (void)seed;
+    // 16-bit deviation store: round to nearest, or stochastically
+    auto store_dev = [&](T* p, R v, uint32_t h, uint32_t pop) {
+        if constexpr (SR)
+            *p = from_real_sr<T>(v, sr_bits(h, pop));
+        else
+            *p = from_real<T, R>(v);
+    };
     const R Dphi = R(dm.Dphi);
     const R De2 = R(dm.Dphi / PL::E2);
     const R qphi = R(dm.qphi);
@@ -229,9 +239,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 #pragma unroll
                         for (int j = 0; j < QU; ++j) fn[(long long)j * n + s] = from_real<T, R>(fv[j]);
                     } else {
+                        const uint32_t h = SR ? sr_hash((uint32_t)s, seed) : 0u;
 #pragma unroll
                         for (int j = 1; j < QU; ++j)
-                            fn[(long long)(j - 1) * n + s] = from_real<T, R>(fv[j] - R(UL::w(j)) * u);
+                            store_dev(&fn[(long long)(j - 1) * n + s], fv[j] - R(UL::w(j)) * u, h, 32u + j);
                     }
                 }
             } else {
@@ -371,9 +382,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 #pragma unroll
             for (int i = 0; i < QG; ++i) gn[(long long)i * n + s] = from_real<T, R>(gnew[i]);
         } else {
+            const uint32_t h = SR ? sr_hash((uint32_t)s, seed) : 0u;
 #pragma unroll
             for (int i = 1; i < QG; ++i)
-                gn[(long long)(i - 1) * n + s] = from_real<T, R>(gnew[i] - R(PL::w(i)) * phinew);
+                store_dev(&gn[(long long)(i - 1) * n + s], gnew[i] - R(PL::w(i)) * phinew, h, (uint32_t)i);
         }
     };
 
@@ -418,7 +430,11 @@ __global__ void __launch_bounds__(TX * TY, 1024 / (TX * TY)) step_kernel(const S
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_next;
     int* counter = args.counters + args.cur;
-    if (blockIdx.x == 0 && threadIdx.x == 0) args.counters[args.cur ^ 1] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        args.counters[args.cur ^ 1] = 0;
+        if constexpr (UsesSR<S>::value)
+            args.counters[2 + (args.cur ^ 1)] = args.counters[2 + args.cur] + 1;  // next step's rounding seed
+    }
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
         __syncthreads();

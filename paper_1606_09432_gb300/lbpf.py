@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("LBPF_LIB") or os.path.join(_HERE, "liblbpf.so")
 LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_ETIMEOUT, LBPF_ENONFINITE, LBPF_ERANGE = 0, -1, -2, -3, -4, -5, -6
 LBPF_D2Q9_D2Q5, LBPF_D3Q15_D3Q7, LBPF_D3Q19_D3Q7, LBPF_D3Q27_D3Q7 = 0, 1, 2, 3
 LBPF_GRAD_DD, LBPF_GRAD_FD = 0, 1
-LBPF_FP64, LBPF_FP32, LBPF_FP32_FP16DEV, LBPF_FP32_BF16DEV = 0, 1, 2, 3
+LBPF_FP64, LBPF_FP32, LBPF_FP32_FP16DEV, LBPF_FP32_BF16DEV, LBPF_FP32_FP16DEV_SR = range(5)
 LBPF_AS_CUBIC100, LBPF_AS_ANGLE, LBPF_AS_Y66, LBPF_AS_HOYT110, LBPF_AS_S111 = 0, 1, 2, 3, 4
 LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
 (LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS,
