@@ -245,17 +245,19 @@ typedef enum {
     LBPF_Q_DEVICE_BYTES = 3,   /* device memory held by the context                  */
     LBPF_Q_LAMBDA = 4,         /* lambda of domain 0 (after the lambda* rule)        */
     LBPF_Q_STEP_KERNELS = 5,   /* step-kernel launches issued by lbpf_step so far     */
-    LBPF_Q_TILE_ROWS = 6,      /* rows of the step kernel's tile (autotuned)          */
-    LBPF_Q_SEGMENT = 7,        /* z-planes per work item of the step kernel (3D)      */
+    LBPF_Q_TILE_ROWS = 6,      /* tile variant of the step kernel (autotuned): 8, 16 */
+    LBPF_Q_SEGMENT = 7,        /* z-planes (3D) or y-rows (2D) per work item          */
     LBPF_Q_BLOCKS = 8          /* resident blocks of the persistent step launch       */
 } lbpf_query_t;
 
 /* Override the work schedule of the step kernel (normally chosen at
- * lbpf_create by a cached or timed autotune, or by rule): tile_rows is 8 or 16
- * (sites of a tile along y; tiles are 32 sites along x), segment the number of
- * z-planes per work item (3D; >= 1, ignored in 2D).  Results do not depend on
- * the schedule; only speed does.  A performance knob with no counterpart in
- * the paper.  Errors: LBPF_EINVAL. */
+ * lbpf_create by a cached or timed autotune, or by rule).  The kernel marches
+ * a tile along z (3D) or y (2D).  tile_rows is 8 or 16: in 3D the tile is 32
+ * sites along x by tile_rows along y; in 2D it is one row of 16 * tile_rows
+ * sites (128 or 256) along x.  segment (>= 1) is the number of z-planes (3D)
+ * or y-rows (2D) per work item.  Results do not depend on the schedule; only
+ * speed does.  A performance knob with no counterpart in the paper.
+ * Errors: LBPF_EINVAL. */
 int lbpf_set_schedule(lbpf_ctx* ctx, int tile_rows, int segment);
 
 /* Read a property of the context into *value. */

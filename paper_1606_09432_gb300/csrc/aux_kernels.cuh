@@ -226,35 +226,35 @@ inline int grid_for(long long n)
 
 template <class PL, class UL, class S>
 struct LauncherImpl {
-    template <int TY>
+    // the step kernel of tile variant V (2D lattices through their XZ view)
+    using KP = KernelLattice<PL>;
+    using KU = KernelLattice<UL>;
+    template <int V> static constexpr int TXV = tile_x(PL::D, V);
+    template <int V> static constexpr int TYV = tile_y(PL::D, V);
+    template <int V> static constexpr auto kernel() { return step_kernel<KP, KU, S, TXV<V>, TYV<V>>; }
+    template <int V> static constexpr size_t smem_v() { return step_smem_bytes<KP, KU, S, TXV<V>, TYV<V>>(); }
+
+    template <int V>
     static cudaError_t step_v(const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        step_kernel<PL, UL, S, TY><<<n_blocks, TX * TY, step_smem_bytes<PL, UL, S, TY>(), s>>>(a);
+        kernel<V>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V>(), s>>>(a);
         return cudaGetLastError();
     }
     static cudaError_t step(int v, const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        return v == 0 ? step_v<kTileRows[0]>(a, n_blocks, s) : step_v<kTileRows[1]>(a, n_blocks, s);
+        return v == 0 ? step_v<0>(a, n_blocks, s) : step_v<1>(a, n_blocks, s);
     }
-    static size_t smem(int v)
-    {
-        return v == 0 ? step_smem_bytes<PL, UL, S, kTileRows[0]>() : step_smem_bytes<PL, UL, S, kTileRows[1]>();
-    }
+    static size_t smem(int v) { return v == 0 ? smem_v<0>() : smem_v<1>(); }
     static cudaError_t prepare(int v)
     {
-        if (v == 0)
-            return cudaFuncSetAttribute(step_kernel<PL, UL, S, kTileRows[0]>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(0));
-        return cudaFuncSetAttribute(step_kernel<PL, UL, S, kTileRows[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem(1));
+        return v == 0 ? cudaFuncSetAttribute(kernel<0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<0>())
+                      : cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
     }
     static int blocks_per_sm(int v)
     {
         int nb = 0;
-        cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                     &nb, step_kernel<PL, UL, S, kTileRows[0]>, TX * kTileRows[0], smem(0))
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                     &nb, step_kernel<PL, UL, S, kTileRows[1]>, TX * kTileRows[1], smem(1));
+        cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<0>(), TXV<0> * TYV<0>, smem_v<0>())
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<1>(), TXV<1> * TYV<1>, smem_v<1>());
         if (e != cudaSuccess) {
             cudaGetLastError();
             return 1;

@@ -119,14 +119,19 @@ static void free_all(lbpf_ctx* c)
 
 
 // ---------------------------------------------------------------------------
-// Work schedule of the step kernel.  Items are columns of TX x TY sites over
-// z-segments, listed segment by segment; the kernel runs as many blocks as
-// fit on the GPU and takes items in order (see step_kernel).
+// Work schedule of the step kernel.  Items are columns of tile_x x tile_y
+// sites over segments of the marched axis (z in 3D, y in 2D), listed segment
+// by segment; the kernel runs as many blocks as fit on the GPU and takes items
+// in order (see step_kernel).
 // ---------------------------------------------------------------------------
-static long long column_units(const lbpf_ctx* c, int ty)
+static long long column_units(const lbpf_ctx* c, int v)
 {
+    const int tx = tile_x(c->dim, v), ty = tile_y(c->dim, v);
     long long units = 0;
-    for (const DomainDev& d : c->dd) units += (long long)((d.nx + TX - 1) / TX) * ((d.ny + ty - 1) / ty) * d.nz;
+    for (const DomainDev& d : c->dd) {
+        const int ny = c->dim == 3 ? d.ny : 1, nz = c->dim == 3 ? d.nz : d.ny;
+        units += (long long)((d.nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * nz;
+    }
     return units;
 }
 
@@ -136,26 +141,28 @@ static int default_segment(const lbpf_ctx* c, int v)
 {
     if (LBPF_SEGMENT > 0) return LBPF_SEGMENT;
     const double G = (double)c->L->blocks_per_sm(v) * c->sms;
-    int L = (int)std::lround(std::sqrt(5.0 * (double)column_units(c, kTileRows[v]) / G));
+    int L = (int)std::lround(std::sqrt(5.0 * (double)column_units(c, v) / G));
     return L < 8 ? 8 : (L > 256 ? 256 : L);
 }
 
 static int set_schedule(lbpf_ctx* c, int v, int seg)
 {
-    const int ty = kTileRows[v];
+    const int wx = tile_x(c->dim, v), wy = tile_y(c->dim, v);
     std::vector<WorkItem> items;
     for (int k = 0; k < c->n_domains; ++k) {
         const DomainDev& d = c->dd[k];
-        const int tx = (d.nx + TX - 1) / TX, tyn = (d.ny + ty - 1) / ty;
-        const int nseg = c->dim == 3 ? (d.nz + seg - 1) / seg : 1;
+        // 2D: the kernel marches the y axis (its z) with one-row tiles
+        const int ny = c->dim == 3 ? d.ny : 1, nz = c->dim == 3 ? d.nz : d.ny;
+        const int tx = (d.nx + wx - 1) / wx, tyn = (ny + wy - 1) / wy;
+        const int nseg = (nz + seg - 1) / seg;
         for (int sg = 0; sg < nseg; ++sg) {
-            const int z0 = (int)((long long)sg * d.nz / nseg), z1 = (int)((long long)(sg + 1) * d.nz / nseg);
+            const int z0 = (int)((long long)sg * nz / nseg), z1 = (int)((long long)(sg + 1) * nz / nseg);
             for (int by = 0; by < tyn; ++by)
                 for (int bx = 0; bx < tx; ++bx) {
                     WorkItem w;
                     w.dom = k;
-                    w.x0 = bx * TX;
-                    w.y0 = by * ty;
+                    w.x0 = bx * wx;
+                    w.y0 = by * wy;
                     w.z0 = z0;
                     w.z1 = z1;
                     w.pad = 0;
@@ -759,7 +766,7 @@ extern "C" int lbpf_query(const lbpf_ctx* c, int what, double* value)
     case LBPF_Q_LAMBDA: v = c->dd[0].lambda; break;
     case LBPF_Q_STEP_KERNELS: v = (double)c->kernels; break;
     case LBPF_Q_TILE_ROWS: v = kTileRows[c->tile_v]; break;
-    case LBPF_Q_SEGMENT: v = c->dim == 3 ? c->seg_len : 1; break;
+    case LBPF_Q_SEGMENT: v = c->seg_len; break;
     case LBPF_Q_BLOCKS: v = c->n_blocks; break;
     default: return fail(const_cast<lbpf_ctx*>(c), LBPF_EINVAL, "lbpf_query: unknown property %d", what);
     }

@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/lbpf.h"
 
 namespace lbpf {
@@ -230,12 +232,35 @@ struct StepArgs {
     int grad;   // LBPF_GRAD_DD / LBPF_GRAD_FD
 };
 
-// Tile of one thread block of the step kernel: TX x TY sites per z-plane, one
-// thread per site of the tile.  TY is a template parameter of the kernel; the
-// context picks one of kTileRows (autotuned).
+// Tile of one thread block of the step kernel, one thread per site of a tile
+// plane; the context picks variant v (autotuned):
+//   3D: TX x kTileRows[v] sites of an xy-plane, marching along z;
+//   2D: one row of kStripX[v] sites along x, marching along y (the kernel sees
+//       the 2D lattice in its xz-plane, see XZ below).
 constexpr int TX = 32;
 constexpr int kNumTileVariants = 2;
 constexpr int kTileRows[kNumTileVariants] = {8, 16};
+constexpr int kStripX[kNumTileVariants] = {128, 256};
+constexpr int tile_x(int dim, int v) { return dim == 3 ? TX : kStripX[v]; }
+constexpr int tile_y(int dim, int v) { return dim == 3 ? kTileRows[v] : 1; }
+
+// A 2D lattice seen by the step kernel in its xz-plane (e_y -> e_z), so that
+// the kernel marches along the physical y axis as it marches along z in 3D and
+// needs no halo across the strip (which is one row high).
+template <class L> struct XZ {
+    static_assert(L::D == 2, "XZ views a 2D lattice");
+    static constexpr int D = 3, Q = L::Q;
+    static constexpr bool xz = true;
+    static constexpr double E2 = L::E2;
+    LBPF_HD static constexpr int ex(int i) { return L::ex(i); }
+    LBPF_HD static constexpr int ey(int) { return 0; }
+    LBPF_HD static constexpr int ez(int i) { return L::ey(i); }
+    LBPF_HD static constexpr double w(int i) { return L::w(i); }
+};
+template <class L, class = void> struct IsXZ { static constexpr bool value = false; };
+template <class L> struct IsXZ<L, decltype(void(L::xz))> { static constexpr bool value = L::xz; };
+// Lattice the step kernel is instantiated with.
+template <class L> using KernelLattice = typename std::conditional<L::D == 2, XZ<L>, L>::type;
 
 // Index of the direction opposite to i on lattice L.
 template <class L>

@@ -25,12 +25,14 @@
 // (Feq_Phase), eta_phi of Eq. (LBE_RelaxationTime) and Q_phi of Eq.
 // (LBE_SourceTerm), all evaluated at the collision node x.
 //
-// Tiling: a block owns a TX x TY column of sites and marches along z over
+// Tiling: a block owns a TXT x TY column of sites and marches along z over
 // [z0, z1), keeping rings of planes in shared memory: phi^n and
 // h = aux + phi^n / 2 on the tile plus a 2-site halo, and the collision
 // coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
 // is read from HBM once per launch except the halo rims, which neighbouring
-// blocks share through L2.
+// blocks share through L2.  A 2D domain is run through the same march with
+// its y axis as the kernel's z axis (lattice XZ<>): the tile is one row of
+// TXT sites, without halo rows.
 #pragma once
 
 #include "lbpf_internal.cuh"
@@ -91,18 +93,21 @@ template <> struct CoefIO<double> {
 };
 
 // One work item: the column (x0, y0) of one domain over planes [z0, z1).
-template <class PL, class UL, class S, int TY>
+template <class PL, class UL, class S, int TXT, int TY>
 __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
-    constexpr int NT = TX * TY;
+    static_assert(PL::D == 3 && UL::D == 3, "the step kernel marches along z (2D lattices through XZ)");
+    constexpr int NT = TXT * TY;
     using R = typename S::Real;
     using T = typename S::T;
     constexpr int D = PL::D;
-    constexpr int RX = TX + 4, RY = TY + 4, RP = RX * RY;  // tile + 2-site halo
-    constexpr int CX = TX + 2, CY = TY + 2, CP = CX * CY;  // tile + 1-site halo
-    constexpr int NPH = D == 3 ? 4 : 1;                     // phi / index ring depth
-    constexpr int NH = D == 3 ? 3 : 1;                      // h ring depth
-    constexpr int NC = D == 3 ? 3 : 1;                      // coefficient ring depth
+    constexpr bool XZV = IsXZ<PL>::value;                   // 2D domain, y marched as z
+    constexpr int HL = XZV ? 0 : 2, HC = XZV ? 0 : 1;       // halo rows (y) of the phi and coefficient planes
+    constexpr int RX = TXT + 4, RY = TY + 2 * HL, RP = RX * RY;  // tile + 2-site halo
+    constexpr int CX = TXT + 2, CY = TY + 2 * HC, CP = CX * CY;  // tile + 1-site halo
+    constexpr int NPH = 4;                                  // phi / index ring depth
+    constexpr int NH = 3;                                   // h ring depth
+    constexpr int NC = 3;                                   // coefficient ring depth
     constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
     constexpr int QG = PL::Q, QU = UL::Q;
     constexpr bool DEV = S::dev;
@@ -115,11 +120,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * NCO * CP);
 
     const DomainDev& dm = args.doms[it.dom];
-    const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
+    const int nx = dm.nx, ny = XZV ? 1 : dm.ny, nz = XZV ? dm.ny : dm.nz;
     const long long n = dm.n;
     const long long nxy = (long long)nx * ny;
     const int x0 = it.x0, y0 = it.y0;
-    const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
+    const int tw = min(TXT, nx - x0), th = min(TY, ny - y0);
     const int tid = threadIdx.x;
     const bool collide = args.collide != 0;
     const bool use_index = dm.use_index != 0;
@@ -169,11 +174,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         R* dphi = s_phi + sphi(zp) * RP;
         R* dh = s_h + sh(zp) * RP;
         int8_t* dI = s_I + sphi(zp) * RP;
-        const int rows = th + 4;
+        const int rows = th + 2 * HL;
         for (int k = tid; k < RX * rows; k += NT) {
             const int ly = k / RX, lx = k - ly * RX;
             if (lx >= tw + 4) continue;
-            const long long s = zo + (long long)wrapy(y0 + ly - 2) * nx + wrapx(x0 + lx - 2);
+            const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
             const R ph = phic[s];
             dphi[k] = ph;
             if (need_h) dh[k] = auxc[s] + R(0.5) * ph;
@@ -190,14 +195,14 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const int zm = wrapz(zp - 1), zq = wrapz(zp + 1);
         const long long ozm = (long long)(zm - zw) * nxy, ozp = (long long)(zq - zw) * nxy;
         R* dco = s_co + sco(zp) * NCO * CP;
-        const int rows = th + 2;
+        const int rows = th + 2 * HC;
         for (int k = tid; k < CX * rows; k += NT) {
             const int ly = k / CX, lx = k - ly * CX;
             if (lx >= tw + 2) continue;
-            const int px = lx + 1, py = ly + 1;  // position in the halo-2 frame
-            const int gx = wrapx(x0 + lx - 1), gy = wrapy(y0 + ly - 1);
+            const int px = lx + 1, py = ly + HL - HC;  // position in the phi frame
+            const int gx = wrapx(x0 + lx - 1), gy = wrapy(y0 + ly - HC);
             const long long s = zo + (long long)gy * nx + gx;
-            const bool inner = store && lx >= 1 && lx <= tw && ly >= 1 && ly <= th;
+            const bool inner = store && lx >= 1 && lx <= tw && ly >= HC && ly < th + HC;
             const R ph = s_phi[sphi(zp) * RP + py * RX + px];
 
             // offsets of the periodic neighbours of s
@@ -279,9 +284,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             } else {
                 const R* pl = s_phi + sphi(zp) * RP;
                 Gx = R(0.5) * (pl[py * RX + px + 1] - pl[py * RX + px - 1]);
-                Gy = R(0.5) * (pl[(py + 1) * RX + px] - pl[(py - 1) * RX + px]);
-                if (D == 3)
-                    Gz = R(0.5) * (s_phi[sphi(zp + 1) * RP + py * RX + px] - s_phi[sphi(zp - 1) * RP + py * RX + px]);
+                if (!XZV) Gy = R(0.5) * (pl[(py + 1) * RX + px] - pl[(py - 1) * RX + px]);
+                Gz = R(0.5) * (s_phi[sphi(zp + 1) * RP + py * RX + px] - s_phi[sphi(zp - 1) * RP + py * RX + px]);
             }
 
             // crystal index (Sec. 4.3): keep a non-zero index; otherwise take
@@ -303,7 +307,14 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             }
 
             R a = 1, Nx = 0, Ny = 0, Nz = 0;
-            if (cryst > 0 && cryst <= dm.n_crystals) anisotropy<R, D>(dm.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
+            if (cryst > 0 && cryst <= dm.n_crystals) {
+                if (XZV) {  // physical (x, y) = kernel (x, z)
+                    R n2 = 0;
+                    anisotropy<R, 2>(dm.cr[cryst - 1], Gx, Gz, R(0), a, Nx, Nz, n2);
+                } else {
+                    anisotropy<R, D>(dm.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
+                }
+            }
 
             const R A2 = a * a;
             const R iA2 = recip<R>(A2);
@@ -318,7 +329,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 
     // -- phase-field collision + streaming for the tile interior of plane z ----
     auto output_plane = [&](int z) {
-        const int ltx = tid % TX, lty = tid / TX;
+        const int ltx = tid % TXT, lty = tid / TXT;
         if (ltx >= tw || lty >= th) return;
         const int gx = x0 + ltx, gy = y0 + lty;
         const long long s = (long long)z * nxy + (long long)gy * nx + gx;
@@ -335,8 +346,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             return (ex < 0 ? oxm : (ex > 0 ? oxp : 0)) + (ey < 0 ? oym : (ey > 0 ? oyp : 0)) +
                    (D == 3 ? (ez < 0 ? ozm : (ez > 0 ? ozp : 0)) : 0);
         };
-        const int px = ltx + 2, py = lty + 2;  // halo-2 frame
-        const int cx = ltx + 1, cy = lty + 1;  // halo-1 frame
+        const int px = ltx + 2, py = lty + HL;  // phi frame
+        const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
         R gl[QG];
         if (!DEV) {
 #pragma unroll
@@ -389,13 +400,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         }
     };
 
-    if constexpr (D == 2) {
-        load_plane(0);
-        __syncthreads();
-        coef_plane(0, true);
-        __syncthreads();
-        output_plane(0);
-    } else {
+    {
         const int z0 = it.z0, z1 = it.z1;
         load_plane(z0 - 2);
         load_plane(z0 - 1);
@@ -424,8 +429,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 // The launch uses counter[cur] and clears counter[cur ^ 1] for the next step
 // (launches on one stream run in order; cur alternates every step).
 // Launch bounds ask for 1024 resident threads per SM (64 registers a thread).
-template <class PL, class UL, class S, int TY>
-__global__ void __launch_bounds__(TX * TY, 1024 / (TX * TY)) step_kernel(const StepArgs args)
+template <class PL, class UL, class S, int TXT, int TY>
+__global__ void __launch_bounds__(TXT * TY, 1024 / (TXT * TY)) step_kernel(const StepArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_next;
@@ -440,18 +445,18 @@ __global__ void __launch_bounds__(TX * TY, 1024 / (TX * TY)) step_kernel(const S
         __syncthreads();
         const int k = s_next;
         if (k >= args.n_items) break;
-        step_item<PL, UL, S, TY>(args, args.items[k], smem_raw);
+        step_item<PL, UL, S, TXT, TY>(args, args.items[k], smem_raw);
         __syncthreads();
     }
 }
 
-template <class PL, class UL, class S, int TY>
+template <class PL, class UL, class S, int TXT, int TY>
 constexpr size_t step_smem_bytes()
 {
     using R = typename S::Real;
-    constexpr int D = PL::D;
-    constexpr int RP = (TX + 4) * (TY + 4), CP = (TX + 2) * (TY + 2);
-    constexpr int NPH = D == 3 ? 4 : 1, NH = D == 3 ? 3 : 1, NC = D == 3 ? 3 : 1, NCO = 6;
+    constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
+    constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
+    constexpr int NPH = 4, NH = 3, NC = 3, NCO = 6;
     return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (size_t)NPH * RP;
 }
 
