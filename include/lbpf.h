@@ -177,9 +177,10 @@ int lbpf_write_fields(lbpf_ctx* ctx, int domain, const void* phi, const void* u,
  * with Q_u = (phi(t + dt) - phi(t)) / (2 dt), one kernel launch for all
  * domains.  On a non-default stream, runs of 16 steps are replayed from CUDA
  * graphs captured on first use (do not call lbpf_step while another capture
- * is active on the context's stream).  Asynchronous on the context's stream;
- * launch errors are returned, device errors surface at the next
- * synchronising call. */
+ * is active on the context's stream).  Asynchronous on the context's stream
+ * (except the first call of a context whose schedule is timed, see
+ * lbpf_set_schedule); launch errors are returned, device errors surface at
+ * the next synchronising call. */
 int lbpf_step(lbpf_ctx* ctx, int n_steps);
 
 typedef enum {
@@ -250,8 +251,12 @@ typedef enum {
     LBPF_Q_BLOCKS = 8          /* resident blocks of the persistent step launch       */
 } lbpf_query_t;
 
-/* Override the work schedule of the step kernel (normally chosen at
- * lbpf_create by a cached or timed autotune, or by rule).  The kernel marches
+/* Override the work schedule of the step kernel.  Normally lbpf_create takes
+ * a choice cached for the configuration (file LBPF_TUNE_CACHE, default
+ * ~/.cache/lbpf_tune.txt) or a rule; configurations of >= 4e6 sites (or any,
+ * with LBPF_AUTOTUNE=1; none with LBPF_AUTOTUNE=0) are then timed at the
+ * first lbpf_step, on the live state, which that call leaves unchanged (it
+ * synchronises the stream once and caches the choice).  The kernel marches
  * a tile along z (3D) or y (2D).  tile_rows is 8 or 16: in 3D the tile is 32
  * sites along x by tile_rows along y; in 2D it is one row of 16 * tile_rows
  * sites (128 or 256) along x.  segment (>= 1) is the number of z-planes (3D)

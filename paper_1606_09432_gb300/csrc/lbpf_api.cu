@@ -6,6 +6,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+
+#include <sys/stat.h>
 #include <vector>
 
 #include "lbpf_internal.cuh"
@@ -45,6 +47,7 @@ struct lbpf_ctx {
     cudaGraphExec_t graphs[8] = {};
     bool graphs_off = false;
     std::string tuned;  // how the schedule was chosen
+    bool tune_pending = false;  // time the schedules at the first step (on the seeded state)
     // measurement history: per domain a ring of kHistCap entries (t, tip6)
     double* d_hist = nullptr;
     std::vector<int> hist_count, hist_last;
@@ -201,7 +204,7 @@ static std::string tune_key(const lbpf_ctx* c)
             h ^= (unsigned long long)(unsigned)v;
             h *= 1099511628211ULL;
         }
-    snprintf(buf, sizeof(buf), "lat%d-prec%d-grad%d-dom%d-%016llx-sm%d", c->lattice, c->precision, c->grad,
+    snprintf(buf, sizeof(buf), "s2-lat%d-prec%d-grad%d-dom%d-%016llx-sm%d", c->lattice, c->precision, c->grad,
              c->n_domains, h, c->sms);
     return buf;
 }
@@ -214,7 +217,9 @@ static std::string tune_cache_path()
     return std::string(home ? home : "/tmp") + "/.cache/lbpf_tune.txt";
 }
 
-// Time a few launches of the current schedule (on the zero state).
+// Time a few launches of the current schedule on the live state.  Every trial
+// reads the current buffers (cur, fcur, acur) and writes the other ones,
+// which the next real step overwrites, so the state is left as it was.
 static double time_schedule(lbpf_ctx* c, int launches)
 {
     cudaEvent_t e0, e1;
@@ -227,12 +232,14 @@ static double time_schedule(lbpf_ctx* c, int launches)
     a.items = c->d_items;
     a.n_items = c->n_items;
     a.counters = c->d_counters;
-    a.fcur = a.acur = 0;
+    a.cur = c->cur;
+    a.fcur = c->fcur;
+    a.acur = c->acur;
     a.collide = 1;
     a.grad = c->grad;
     double best = 1e30;
     for (int k = 0; k < launches + 2; ++k) {
-        a.cur = k & 1;
+        if (cudaMemsetAsync(c->d_counters + c->cur, 0, sizeof(int), c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
         if (c->L->step(c->tile_v, a, c->n_blocks, c->stream) != cudaSuccess) break;
         cudaEventRecord(e1, c->stream);
@@ -247,14 +254,13 @@ static double time_schedule(lbpf_ctx* c, int launches)
     return best;
 }
 
-// Pick the tile variant and segment length: from the cache file, else by
-// timing the candidates on large contexts (the state is all zeros at this
-// point and stays zero: every update of a zero state is zero), else by rule.
-static int choose_schedule(lbpf_ctx* c)
+// Schedule at context creation: a cached choice for this configuration, else
+// the rule (tile variant 0, default segment); large configurations (or
+// LBPF_AUTOTUNE=1) are then timed at the first step, on the seeded state.
+static int initial_schedule(lbpf_ctx* c)
 {
     const std::string key = tune_key(c);
-    const std::string path = tune_cache_path();
-    if (FILE* f = fopen(path.c_str(), "r")) {
+    if (FILE* f = fopen(tune_cache_path().c_str(), "r")) {
         char k[200];
         int v, seg;
         while (fscanf(f, "%199s %d %d", k, &v, &seg) == 3)
@@ -268,32 +274,39 @@ static int choose_schedule(lbpf_ctx* c)
     double sites = 0;
     for (const DomainDev& d : c->dd) sites += (double)d.n;
     const char* env = getenv("LBPF_AUTOTUNE");
-    const bool tune = env ? atoi(env) != 0 : sites >= 4e6;
-    int best_v = 0, best_seg = default_segment(c, best_v);
-    if (tune) {
-        double best_t = 1e30;
-        for (int v = 0; v < kNumTileVariants; ++v) {
-            const int L0 = default_segment(c, v);
-            const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
-            for (int j = 0; j < (c->dim == 3 ? 3 : 1); ++j) {
-                int rc = set_schedule(c, v, segs[j]);
-                if (rc) return rc;
-                const double t = time_schedule(c, 4);
-                if (t < best_t) {
-                    best_t = t;
-                    best_v = v;
-                    best_seg = segs[j];
-                }
+    c->tune_pending = env ? atoi(env) != 0 : sites >= 4e6;
+    c->tuned = "rule";
+    return set_schedule(c, 0, default_segment(c, 0));
+}
+
+// Time tile variants x segments {L, L/2, 2L} and keep (and cache) the fastest.
+static int autotune(lbpf_ctx* c)
+{
+    CK(cudaStreamSynchronize(c->stream));
+    double best_t = 1e30;
+    int best_v = c->tile_v, best_seg = c->seg_len;
+    for (int v = 0; v < kNumTileVariants; ++v) {
+        const int L0 = default_segment(c, v);
+        const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
+        for (int j = 0; j < 3; ++j) {
+            int rc = set_schedule(c, v, segs[j]);
+            if (rc) return rc;
+            const double t = time_schedule(c, 4);
+            if (t < best_t) {
+                best_t = t;
+                best_v = v;
+                best_seg = segs[j];
             }
         }
-        CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 4, c->stream));
-        c->tuned = "timed";
-        if (FILE* f = fopen(path.c_str(), "a")) {
-            fprintf(f, "%s %d %d\n", key.c_str(), best_v, best_seg);
-            fclose(f);
-        }
-    } else {
-        c->tuned = "rule";
+    }
+    CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream));
+    c->tuned = "timed";
+    const std::string path = tune_cache_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // e.g. ~/.cache
+    if (FILE* f = fopen(path.c_str(), "a")) {
+        fprintf(f, "%s %d %d\n", tune_key(c).c_str(), best_v, best_seg);
+        fclose(f);
     }
     return set_schedule(c, best_v, best_seg);
 }
@@ -431,7 +444,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
     }
     if (rc == LBPF_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(c, LBPF_ECUDA, "lbpf_create: stream synchronisation failed");
-    if (rc == LBPF_OK) rc = choose_schedule(c);
+    if (rc == LBPF_OK) rc = initial_schedule(c);
     if (rc != LBPF_OK) {
         t_err = c->err;
         free_all(c);
@@ -593,6 +606,10 @@ extern "C" int lbpf_step(lbpf_ctx* c, int n_steps)
     int rc = check_ctx(c, 0);
     if (rc) return rc;
     if (n_steps < 0) return fail(c, LBPF_EINVAL, "lbpf_step: n_steps < 0");
+    if (c->tune_pending && n_steps > 0) {
+        c->tune_pending = false;
+        if ((rc = autotune(c))) return rc;
+    }
     // graphs need a capturable stream (not the legacy default stream)
     const bool graphs = c->stream != nullptr && !c->graphs_off;
     while (n_steps > 0) {
@@ -739,6 +756,8 @@ extern "C" int lbpf_set_schedule(lbpf_ctx* c, int tile_rows, int segment)
         if (kTileRows[k] == tile_rows) v = k;
     if (v < 0 || segment < 1) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: tile_rows must be 8 or 16, segment >= 1");
     CK(cudaStreamSynchronize(c->stream));
+    c->tune_pending = false;
+    c->tuned = "set";
     return set_schedule(c, v, segment);
 }
 

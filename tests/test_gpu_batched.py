@@ -88,6 +88,26 @@ def test_schedules_give_identical_results(L, lattice, shape):
         L.lbpf_set_schedule(s.ctx, 12, 8)
 
 
+@pytest.mark.parametrize("lattice,shape", [(1, (36, 40, 44)), (0, (1, 90, 130))])
+def test_autotune_at_first_step_leaves_state(L, tmp_path, monkeypatch, lattice, shape):
+    """The schedule trials run at the first step on the live state: the run
+    is bit-identical to one with the rule schedule and no trials, and the
+    choice is cached for the next context of the same configuration."""
+    prm = dict(W.C3D_PARAMS, delta=0.3) if lattice == 1 else W.C1_PARAMS
+    seeds = [(shape[2] / 2, shape[1] / 2, shape[0] / 2, 6.0, 0)]
+    cr = [dict(kind=0, eps=0.05)]
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("LBPF_TUNE_CACHE", str(cache))
+    runs = []
+    for tune in ("1", "0"):
+        monkeypatch.setenv("LBPF_AUTOTUNE", tune)
+        s = gpu_run(L, lattice, shape, prm, cr, seeds=seeds, precision=L.LBPF_FP32)
+        s.step(25)
+        runs.append(s.fields())
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert cache.exists() and len(cache.read_text().split()) == 3
+
+
 def test_batch64_workload_invariants(L):
     """The 64-domain batched 2D configuration at full size (24.4 M sites), FP32:
     per-domain conservation of sum(u - phi/2) and growth, after 300 steps."""
