@@ -225,6 +225,8 @@ def run_reference(args):
 
 
 def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
+    K, M, kv, alpha = args.sur_k, args.sur_m, args.sur_kv, args.sur_alpha
+    n_draws, traj = args.sur_draws, args.sur_traj
     """Surrogate + LB vs plain LB on one 2D domain of the batched
     configuration's distributions: same final time, tip velocity from the
     last LB measurements, wall-clock time to solution."""
@@ -236,9 +238,10 @@ def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
     from paper_1606_09432_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
-    X, Y = S.generate_pairs(W.surrogate_draws(16, size=train_size, seed=7), 2000, 50, torch)
+    X, Y = S.generate_pairs(W.surrogate_draws(n_draws, size=train_size, seed=7), traj, K, torch)
     net = L.Net(train_size, train_size, batch=8, seed=1)
-    hist = S.train(net, X, Y, 1500, lr=1e-3, torch=torch)
+    net.set_loss_weight(alpha)
+    hist = S.train(net, X, Y, args.sur_train, lr=1e-3, torch=torch)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     d = W.surrogate_draws(1, size=size, seed=99)[0]
@@ -267,7 +270,7 @@ def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t1
     sc = solver()
-    ctl = S.Controller(sc, inf, d, centre, torch, K=50, M=4, kv=20)
+    ctl = S.Controller(sc, inf, d, centre, torch, K=K, M=M, kv=kv)
     st = ctl.run(steps_total)
     v_plain, v_sur = tipv(sp), tipv(sc)
     xx = torch.zeros((1, size, size, 5), device="cuda")
@@ -282,12 +285,16 @@ def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
     line = {"metric": "surrogate + LB vs plain LB time to solution", "value": round(t_plain / st.seconds, 4),
             "unit": "x (plain LB time / surrogate+LB time)", "higher_is_better": True, "n_gpus": 1,
             "config": {"workload": f"2D {size}^2 periodic, D2Q9/D2Q5 FP32, one seed R=10, {steps_total} steps, "
-                                   f"K=50, M=4, k_v=20, network trained on 16 draws at {train_size}^2"},
+                                   f"K={K}, M={M}, k_v={kv}, network trained on {n_draws} draws at {train_size}^2 "
+                                   f"({traj} LB steps each, pairs every K steps, {args.sur_train} Adam steps, "
+                                   f"interface loss weight {alpha})"},
             "plain_lb_s": round(t_plain, 4), "surrogate_lb_s": round(st.seconds, 4),
             "jumps_accepted": st.jumps_accepted, "blocks_rejected": st.blocks_rejected,
             "tip_velocity_rel_err": round(abs(v_sur - v_plain) / abs(v_plain), 4) if v_plain else None,
             "net_forward_ms": round(t_net * 1e3, 3), "train_s": round(t_train, 2),
-            "train_loss_last": float(np.mean(hist[-50:])), "predict_zero_loss": float((Y ** 2).mean().item())}
+            "train_loss_last": float(np.mean(hist[-50:])), "predict_zero_loss": float((Y ** 2).mean().item()),
+            "rejected_range": st.rejected_range, "rejected_velocity": st.rejected_velocity,
+            "v_dev_median": float(np.median(np.abs(st.v_dev))) if st.v_dev else None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -302,6 +309,13 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="override the cube edge of the workload (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sur-k", type=int, default=50, help="surrogate jump length K (LB steps)")
+    ap.add_argument("--sur-m", type=int, default=4, help="surrogate jumps per validation")
+    ap.add_argument("--sur-kv", type=int, default=20, help="LB validation steps after M jumps")
+    ap.add_argument("--sur-alpha", type=float, default=0.0, help="interface weight of the training loss")
+    ap.add_argument("--sur-draws", type=int, default=16, help="training draws")
+    ap.add_argument("--sur-traj", type=int, default=2000, help="LB steps per training trajectory")
+    ap.add_argument("--sur-train", type=int, default=1500, help="Adam steps")
     ap.add_argument("--surrogate", action="store_true",
                     help="time-to-solution of surrogate + LB vs plain LB (trains a network first)")
     args = ap.parse_args()

@@ -322,8 +322,15 @@ int lbpf_net_forward(lbpf_net* net, const float* x, float* y);
  * lbpf_net_get_params(which = 1)). */
 int lbpf_net_backward(lbpf_net* net, const float* dy);
 /* One Adam step (beta 0.9, 0.999) on the mean squared error to `target`
- * (N, H, W, 2); *loss (may be NULL) receives the loss before the step. */
+ * (N, H, W, 2), weighted per site (see lbpf_net_set_loss_weight); *loss (may
+ * be NULL) receives the loss before the step. */
 int lbpf_net_train_step(lbpf_net* net, const float* x, const float* target, float lr, double* loss);
+/* Weight of the training loss: each squared error counts 1 + alpha *
+ * max(0, 1 - phi^2) times, phi the input phase field of its site, so that the
+ * interface (where a jump changes the fields) outweighs the bulk.  alpha = 0
+ * (the default) is the plain mean squared error.  Not in the paper.
+ * Errors: LBPF_EINVAL (NULL net, alpha < 0 or NaN). */
+int lbpf_net_set_loss_weight(lbpf_net* net, float alpha);
 /* Network input from fields: x[p] = (phi, u, cos 4 theta, sin 4 theta, eps)
  * of the crystal I = index[p] (1 everywhere when index is NULL; zeros for
  * I = 0 or I > n_crystals), crystal_tab[2 (I-1)] = eps, [2 (I-1) + 1] = theta. */

@@ -174,6 +174,16 @@ def backward(p, c, dout, emulate=False):
     return np.concatenate(flat)
 
 
+def weighted_mse(out, target, x, alpha=0.0):
+    """Training loss and its gradient in out: mean over all values of
+    w (out - target)^2, w = 1 + alpha max(0, 1 - phi^2) with phi = x[..., 0]
+    the input phase field of the value's site."""
+    w = 1.0 + alpha * np.maximum(0.0, 1.0 - np.asarray(x, np.float64)[..., :1] ** 2)
+    d = np.asarray(out, np.float64) - target
+    n = d.size
+    return float((w * d * d).sum() / n), 2.0 * w * d / n
+
+
 def init_params(seed, scale_head=1e-2):
     rng = np.random.default_rng(seed)
     parts = []

@@ -433,15 +433,23 @@ cudaError_t conv1x1_bwd(const float* x, const float* dy, const float* w, float* 
     return cudaGetLastError();
 }
 
-// Mean squared error over n values: loss[0] += sum (p - t)^2 / n (FP64 atomics
-// per block), dp = 2 (p - t) / n.
-__global__ void mse_kernel(const float* p, const float* t, float* dp, double* loss, long long n)
+// Weighted mean squared error over n values (cout per site): loss[0] +=
+// sum w (p - t)^2 / n (FP64 atomics per block), dp = 2 w (p - t) / n, with
+// w = 1 + alpha max(0, 1 - phi^2) and phi = x[site * cin] the input phase
+// field of the value's site (alpha = 0: plain mean squared error).
+__global__ void mse_kernel(const float* p, const float* t, const float* x, int cin, int cout, float alpha, float* dp,
+                           double* loss, long long n)
 {
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = p[i] - t[i];
-        dp[i] = 2.f * d / (float)n;
-        acc += (double)d * d;
+        float w = 1.f;
+        if (alpha > 0.f) {
+            const float ph = x[(i / cout) * cin];
+            w += alpha * fmaxf(0.f, 1.f - ph * ph);
+        }
+        dp[i] = 2.f * w * d / (float)n;
+        acc += (double)w * d * d;
     }
     __shared__ double red[256];
     red[threadIdx.x] = acc;
@@ -453,9 +461,10 @@ __global__ void mse_kernel(const float* p, const float* t, float* dp, double* lo
     if (threadIdx.x == 0) atomicAdd(loss, red[0] / (double)n);
 }
 
-cudaError_t mse(const float* p, const float* t, float* dp, double* loss, long long n, cudaStream_t s)
+cudaError_t mse(const float* p, const float* t, const float* x, int cin, int cout, float alpha, float* dp, double* loss,
+                long long n, cudaStream_t s)
 {
-    mse_kernel<<<eblocks(n) < 304 ? eblocks(n) : 304, 256, 0, s>>>(p, t, dp, loss, n);
+    mse_kernel<<<eblocks(n) < 304 ? eblocks(n) : 304, 256, 0, s>>>(p, t, x, cin, cout, alpha, dp, loss, n);
     return cudaGetLastError();
 }
 

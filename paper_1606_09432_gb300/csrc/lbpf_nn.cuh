@@ -25,7 +25,8 @@ cudaError_t conv1x1_fwd(const float* x, const float* w, const float* b, float* y
                         cudaStream_t s);
 cudaError_t conv1x1_bwd(const float* x, const float* dy, const float* w, float* dx, float* dw, float* db, long long P,
                         int cin, int cout, cudaStream_t s);
-cudaError_t mse(const float* p, const float* t, float* dp, double* loss, long long n, cudaStream_t s);
+cudaError_t mse(const float* p, const float* t, const float* x, int cin, int cout, float alpha, float* dp, double* loss,
+                long long n, cudaStream_t s);
 cudaError_t adam(float* w, const float* g, float* m, float* v, __nv_bfloat16* wb, long long n, float lr, float b1,
                  float b2, float eps, int t, cudaStream_t s);
 cudaError_t to_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t s);

@@ -38,6 +38,7 @@ struct lbpf_net {
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 params, grads, Adam moments
     __nv_bfloat16* pb = nullptr;  // BF16 copy of all params (only 3x3 parts used)
     int adam_t = 0;
+    float loss_alpha = 0.f;  // interface weight of the training loss
     // activations (N, h, w, c) and their gradients
     float *xin, *a1a, *a1, *p1, *a2a, *a2, *p2, *a3a, *a3, *u2, *d2a, *d2, *u1, *d1a, *d1, *out;
     float *g_big0, *g_big1, *g_mid0, *g_mid1, *g_sml0, *g_sml1, *g_cat1, *g_cat2, *g_out;
@@ -322,6 +323,13 @@ extern "C" int lbpf_net_backward(lbpf_net* net, const float* dy)
     return backward(net);
 }
 
+extern "C" int lbpf_net_set_loss_weight(lbpf_net* net, float alpha)
+{
+    if (!net || !(alpha >= 0.f)) return LBPF_EINVAL;
+    net->loss_alpha = alpha;
+    return LBPF_OK;
+}
+
 extern "C" int lbpf_net_train_step(lbpf_net* net, const float* x, const float* target, float lr, double* loss)
 {
     if (!net || !x || !target) return LBPF_EINVAL;
@@ -329,7 +337,7 @@ extern "C" int lbpf_net_train_step(lbpf_net* net, const float* x, const float* t
     if (rc) return rc;
     const long long n = (long long)net->N * net->H * net->W * kOut;
     NK(cudaMemsetAsync(net->d_loss, 0, sizeof(double), net->stream));
-    NK(mse(net->out, target, net->g_out, net->d_loss, n, net->stream));
+    NK(mse(net->out, target, x, kIn, kOut, net->loss_alpha, net->g_out, net->d_loss, n, net->stream));
     NK(cudaMemsetAsync(net->g, 0, sizeof(float) * net->n_params, net->stream));
     if ((rc = backward(net))) return rc;
     net->adam_t += 1;

@@ -31,7 +31,7 @@ EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_
             "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
             "lbpf_net_get_params", "lbpf_net_set_params", "lbpf_net_forward", "lbpf_net_backward",
             "lbpf_net_train_step", "lbpf_net_assemble", "lbpf_net_apply", "lbpf_net_delta",
-            "lbpf_net_range_check"]
+            "lbpf_net_range_check", "lbpf_net_set_loss_weight"]
 
 
 class lbpf_crystal(C.Structure):
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
     lib.lbpf_net_forward.argtypes = [vp, vp, vp]
     lib.lbpf_net_backward.argtypes = [vp, vp]
     lib.lbpf_net_train_step.argtypes = [vp, vp, vp, C.c_float, d]
+    lib.lbpf_net_set_loss_weight.argtypes = [vp, C.c_float]
     lib.lbpf_net_assemble.argtypes = [vp, vp, vp, vp, C.c_int, vp, C.c_longlong, vp]
     lib.lbpf_net_apply.argtypes = [vp, vp, vp, C.c_longlong, vp]
     lib.lbpf_net_delta.argtypes = [vp, vp, vp, vp, vp, C.c_longlong, vp]
@@ -354,6 +355,9 @@ class Net:
     def backward(self, dy):
         self._chk(load().lbpf_net_backward(self.h, _dptr(dy)))
         return self.params(which=1)
+
+    def set_loss_weight(self, alpha):
+        self._chk(load().lbpf_net_set_loss_weight(self.h, float(alpha)))
 
     def train_step(self, x, target, lr):
         loss = C.c_double()

@@ -51,6 +51,26 @@ def test_forward_backward_match_oracle(env):
         off += n + co
 
 
+@pytest.mark.parametrize("alpha", [0.0, 20.0])
+def test_weighted_loss_matches_oracle(env, alpha):
+    """The loss a training step reports (before its update) is the oracle's
+    interface-weighted mean squared error of the oracle's forward pass."""
+    torch, U, L, S, W = env
+    net = L.Net(32, 32, batch=2, seed=6)
+    net.set_loss_weight(alpha)
+    p = net.params().astype(np.float64)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 32, 32, 5)).astype(np.float32)
+    x[..., 0] = np.tanh(2 * x[..., 0])
+    t = (0.05 * rng.standard_normal((2, 32, 32, 2))).astype(np.float32)
+    loss = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), 1e-3)
+    yo, _ = U.forward(p, x.astype(np.float64), emulate=True)
+    lo, _ = U.weighted_mse(yo, t.astype(np.float64), x, alpha)
+    assert abs(loss - lo) <= 1e-2 * lo
+    with pytest.raises(L.LbpfError):
+        net.set_loss_weight(-1.0)
+
+
 def test_training_learns_lb_increments(env):
     torch, U, L, S, W = env
     draws = W.surrogate_draws(12, size=64, seed=11)

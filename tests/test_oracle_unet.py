@@ -77,3 +77,31 @@ def test_backward_matches_finite_differences(U):
         e[i] = h
         fd = (loss(p + e) - loss(p - e)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_weighted_mse_loops_and_gradient(U):
+    """Weighted training loss: a plain loop over sites and channels, the plain
+    mean squared error at alpha = 0, and its gradient by central differences."""
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((2, 3, 4, 5))
+    x[..., 0] = 1.2 * np.tanh(x[..., 0])  # some |phi| > 1: weight clipped at 1
+    out = rng.standard_normal((2, 3, 4, 2))
+    t = rng.standard_normal((2, 3, 4, 2))
+    alpha = 7.0
+    loss, dout = U.weighted_mse(out, t, x, alpha)
+    acc = 0.0
+    for n in range(2):
+        for i in range(3):
+            for j in range(4):
+                ph = x[n, i, j, 0]
+                w = 1.0 + alpha * max(0.0, 1.0 - ph * ph)
+                for c in range(2):
+                    acc += w * (out[n, i, j, c] - t[n, i, j, c]) ** 2
+    assert abs(loss - acc / out.size) < 1e-12
+    assert abs(U.weighted_mse(out, t, x, 0.0)[0] - ((out - t) ** 2).mean()) < 1e-12
+    for k in rng.choice(out.size, 8, replace=False):
+        e = np.zeros(out.size)
+        e[k] = 1e-6
+        e = e.reshape(out.shape)
+        fd = (U.weighted_mse(out + e, t, x, alpha)[0] - U.weighted_mse(out - e, t, x, alpha)[0]) / 2e-6
+        assert abs(fd - dout.ravel()[k]) < 1e-7
