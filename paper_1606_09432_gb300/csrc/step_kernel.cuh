@@ -105,8 +105,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     constexpr int HL = XZV ? 0 : 2, HC = XZV ? 0 : 1;       // halo rows (y) of the phi and coefficient planes
     constexpr int RX = TXT + 4, RY = TY + 2 * HL, RP = RX * RY;  // tile + 2-site halo
     constexpr int CX = TXT + 2, CY = TY + 2 * HC, CP = CX * CY;  // tile + 1-site halo
-    constexpr int NPH = 4;                                  // phi / index ring depth
-    constexpr int NH = 3;                                   // h ring depth
+    constexpr int NPH = 5;                                  // phi / index ring depth (z-1 .. z+3)
+    constexpr int NH = 4;                                   // h ring depth (z .. z+3)
     constexpr int NC = 3;                                   // coefficient ring depth
     constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
     constexpr int QG = PL::Q, QU = UL::Q;
@@ -164,11 +164,49 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     auto wrapx = [&](int v) { return v < 0 ? v + nx : (v >= nx ? v - nx : v); };
     auto wrapy = [&](int v) { return v < 0 ? v + ny : (v >= ny ? v - ny : v); };
     auto wrapz = [&](int v) { return v < 0 ? v + nz : (v >= nz ? v - nz : v); };
-    auto sphi = [&](int zp) { return zp & (NPH - 1); };
-    auto sh = [&](int zp) { return (zp + 3) % NH; };
+    auto sphi = [&](int zp) { return (zp + 2 * NPH) % NPH; };
+    auto sh = [&](int zp) { return (zp + 2 * NH) % NH; };
     auto sco = [&](int zp) { return (zp + 3) % NC; };
 
-    // -- load one plane of phi^n (and h, I) on the tile + 2-site halo ---------
+    // -- asynchronous copy (cp.async) of one plane of phi^n and aux on the
+    // tile + 2-site halo into the rings, issued one plane ahead of its use so
+    // that the loads overlap the coefficient and output phases; finish_plane
+    // then waits for the thread's own copies and forms h = aux + phi^n / 2 in
+    // place on the items that thread copied (a barrier follows before use).
+    auto async_plane = [&](int zp) {
+        const long long zo = (long long)wrapz(zp) * nxy;
+        R* dphi = s_phi + sphi(zp) * RP;
+        R* dh = s_h + sh(zp) * RP;
+        int8_t* dI = s_I + sphi(zp) * RP;
+        const int rows = th + 2 * HL;
+        for (int k = tid; k < RX * rows; k += NT) {
+            const int ly = k / RX, lx = k - ly * RX;
+            if (lx >= tw + 4) continue;
+            const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dphi + k)),
+                         "l"(phic + s), "n"((int)sizeof(R)));
+            if (need_h)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dh + k)),
+                             "l"(auxc + s), "n"((int)sizeof(R)));
+            if (use_index) dI[k] = Ic[s];
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    auto finish_plane = [&](int zp) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!need_h) return;
+        const R* dphi = s_phi + sphi(zp) * RP;
+        R* dh = s_h + sh(zp) * RP;
+        const int rows = th + 2 * HL;
+        for (int k = tid; k < RX * rows; k += NT) {
+            const int ly = k / RX, lx = k - ly * RX;
+            if (lx >= tw + 4) continue;
+            dh[k] += R(0.5) * dphi[k];
+        }
+    };
+
+    // -- load one plane of phi^n (and h, I) on the tile + 2-site halo (the
+    // prologue of a work item) -------------------------------------------------
     auto load_plane = [&](int zp) {
         const long long zo = (long long)wrapz(zp) * nxy;
         R* dphi = s_phi + sphi(zp) * RP;
@@ -405,19 +443,20 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         load_plane(z0 - 2);
         load_plane(z0 - 1);
         load_plane(z0);
-        __syncthreads();
-        coef_plane(z0 - 1, false);
-        __syncthreads();
         load_plane(z0 + 1);
         __syncthreads();
+        coef_plane(z0 - 1, false);
         coef_plane(z0, true);
+        __syncthreads();
+        async_plane(z0 + 2);
         for (int z = z0; z < z1; ++z) {
-            __syncthreads();
-            load_plane(z + 2);
+            finish_plane(z + 2);
+            if (z + 3 <= z1 + 1) async_plane(z + 3);
             __syncthreads();
             coef_plane(z + 1, z + 1 < z1);
             __syncthreads();
             output_plane(z);
+            __syncthreads();
         }
     }
 }
@@ -456,7 +495,7 @@ constexpr size_t step_smem_bytes()
     using R = typename S::Real;
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
     constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
-    constexpr int NPH = 4, NH = 3, NC = 3, NCO = 6;
+    constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
     return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (size_t)NPH * RP;
 }
 
