@@ -279,25 +279,33 @@ static int initial_schedule(lbpf_ctx* c)
     return set_schedule(c, 0, default_segment(c, 0));
 }
 
-// Time tile variants x segments {L, L/2, 2L} and keep (and cache) the fastest.
+// Time tile variants x segments {L, L/2, 2L} and keep (and cache) the
+// fastest, but leave the rule's schedule (variant 0, segment L) only for one
+// at least 3 % faster: short trials at the first step are noisy, and a
+// wrong switch has cost up to 10 % in steady state.
 static int autotune(lbpf_ctx* c)
 {
     CK(cudaStreamSynchronize(c->stream));
-    double best_t = 1e30;
-    int best_v = c->tile_v, best_seg = c->seg_len;
+    double best_t = 1e30, rule_t = 1e30;
+    int best_v = 0, best_seg = default_segment(c, 0);
     for (int v = 0; v < kNumTileVariants; ++v) {
         const int L0 = default_segment(c, v);
         const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
         for (int j = 0; j < 3; ++j) {
             int rc = set_schedule(c, v, segs[j]);
             if (rc) return rc;
-            const double t = time_schedule(c, 4);
+            const double t = time_schedule(c, 6);
+            if (v == 0 && j == 0) rule_t = t;
             if (t < best_t) {
                 best_t = t;
                 best_v = v;
                 best_seg = segs[j];
             }
         }
+    }
+    if (!(best_t < 0.97 * rule_t)) {
+        best_v = 0;
+        best_seg = default_segment(c, 0);
     }
     CK(cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 2, c->stream));
     c->tuned = "timed";

@@ -118,6 +118,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     R* s_h = s_phi + NPH * RP;
     R* s_co = s_h + NH * RP;
     int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * NCO * CP);
+    // 2D, FP32 full storage: the heat populations f^{n-1}_j(x - e_j) of the
+    // next coefficient plane are staged too (copied during the output phase).
+    // In 3D the extra shared memory costs more L1 than the copies save.
+    constexpr bool STF = XZV && sizeof(T) == 4 && !DEV;
+    T* s_f = reinterpret_cast<T*>(s_I + ((NPH * RP + 15) & ~15));
 
     const DomainDev& dm = args.doms[it.dom];
     const int nx = dm.nx, ny = XZV ? 1 : dm.ny, nz = XZV ? dm.ny : dm.nz;
@@ -227,7 +232,26 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     // -- heat update, gradient, anisotropy, collision coefficients ----------
     // on one plane of the tile + 1-site halo; heat outputs of the tile
     // interior are stored when `store` is set.
-    auto coef_plane = [&](int zp, bool store) {
+    // f_j on the phi frame of plane zp - ez_j (the pull sources of
+    // coef_plane(zp)) by cp.async into s_f
+    auto stage_f = [&](int zp) {
+        const int rows = th + 2 * HL;
+        for (int k = tid; k < RX * rows; k += NT) {
+            const int ly = k / RX, lx = k - ly * RX;
+            if (lx >= tw + 4) continue;
+            const long long rowx = (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
+#pragma unroll
+            for (int j = 0; j < QU; ++j) {
+                const long long s = (long long)wrapz(zp - UL::ez(j)) * nxy + rowx;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                 (unsigned)__cvta_generic_to_shared(s_f + j * RP + k)),
+                             "l"(fc + (long long)j * n + s));
+            }
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+
+    auto coef_plane = [&](int zp, bool store, bool staged) {
         const int zw = wrapz(zp);
         const long long zo = (long long)zw * nxy;
         const int zm = wrapz(zp - 1), zq = wrapz(zp + 1);
@@ -269,7 +293,9 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     const long long src = s + off(-ex, -ey, -ez);
                     R fj;
                     if (!DEV) {
-                        fj = om_u * to_real(fc[(long long)j * n + src]) + R(UL::w(j)) * hs;
+                        const R fr = (STF && staged) ? to_real(s_f[j * RP + (py - ey) * RX + (px - ex)])
+                                                     : to_real(fc[(long long)j * n + src]);
+                        fj = om_u * fr + R(UL::w(j)) * hs;
                     } else {
                         const R dj = (j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]);
                         fj = R(UL::w(j)) * hs + om_u * dj;
@@ -445,16 +471,19 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         load_plane(z0);
         load_plane(z0 + 1);
         __syncthreads();
-        coef_plane(z0 - 1, false);
-        coef_plane(z0, true);
+        coef_plane(z0 - 1, false, false);
+        coef_plane(z0, true, false);
         __syncthreads();
         async_plane(z0 + 2);
+        const bool stf = STF && collide;
+        if (stf) stage_f(z0 + 1);
         for (int z = z0; z < z1; ++z) {
             finish_plane(z + 2);
             if (z + 3 <= z1 + 1) async_plane(z + 3);
             __syncthreads();
-            coef_plane(z + 1, z + 1 < z1);
+            coef_plane(z + 1, z + 1 < z1, stf);
             __syncthreads();
+            if (stf && z + 2 <= z1) stage_f(z + 2);
             output_plane(z);
             __syncthreads();
         }
@@ -496,7 +525,9 @@ constexpr size_t step_smem_bytes()
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
     constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
     constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
-    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (size_t)NPH * RP;
+    using T = typename S::T;
+    constexpr size_t stf = IsXZ<PL>::value && sizeof(T) == 4 && !S::dev ? (size_t)UL::Q * RP * sizeof(T) : 0;
+    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) + stf;
 }
 
 }  // namespace lbpf
