@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (description, lattice, precision, n)
     "c2-256-fp32": ("3D single crystal 256^3 periodic, D3Q15/D3Q7, FP32, <100> eps=0.05, Delta=0.3, seed R=8", 1, 1, 256),
+    "c2-256-d3q19-fp32": ("3D single crystal 256^3 periodic, D3Q19/D3Q7, FP32, <100> eps=0.05, Delta=0.3, seed R=8",
+                          2, 1, 256),
+    "c2-256-d3q27-fp32": ("3D single crystal 256^3 periodic, D3Q27/D3Q7, FP32, <100> eps=0.05, Delta=0.3, seed R=8",
+                          3, 1, 256),
     "c3-512-fp16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with FP16 deviation storage, "
                        "<110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 2, 512),
     "c3-512-bf16dev": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with BF16 deviation storage, "

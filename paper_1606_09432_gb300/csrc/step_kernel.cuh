@@ -105,7 +105,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     constexpr int HL = XZV ? 0 : 2, HC = XZV ? 0 : 1;       // halo rows (y) of the phi and coefficient planes
     constexpr int RX = TXT + 4, RY = TY + 2 * HL, RP = RX * RY;  // tile + 2-site halo
     constexpr int CX = TXT + 2, CY = TY + 2 * HC, CP = CX * CY;  // tile + 1-site halo
-    constexpr int NPH = 5;                                  // phi / index ring depth (z-1 .. z+3)
+    // phi / index ring depth: planes z-1 .. z+3 in use while plane z is output;
+    // with deviation storage the output reads phi^n at z-1 while the next
+    // plane's copy (z+4) may already be issued, hence one more slot
+    constexpr int NPH = S::dev ? 6 : 5;
     constexpr int NH = 4;                                   // h ring depth (z .. z+3)
     constexpr int NC = 3;                                   // coefficient ring depth
     constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
@@ -485,7 +488,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             __syncthreads();
             if (stf && z + 2 <= z1) stage_f(z + 2);
             output_plane(z);
-            __syncthreads();
+            // no barrier here: the next writes into the rings (finish z+3,
+            // copy z+4) touch slots no warp still in output_plane(z) reads,
+            // and coef_plane(z+2), which overwrites a coefficient plane that
+            // output_plane(z) reads, comes after the next barrier
         }
     }
 }
@@ -524,7 +530,7 @@ constexpr size_t step_smem_bytes()
     using R = typename S::Real;
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
     constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
-    constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
+    constexpr int NPH = S::dev ? 6 : 5, NH = 4, NC = 3, NCO = 6;
     using T = typename S::T;
     constexpr size_t stf = IsXZ<PL>::value && sizeof(T) == 4 && !S::dev ? (size_t)UL::Q * RP * sizeof(T) : 0;
     return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) + stf;
