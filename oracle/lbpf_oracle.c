@@ -602,8 +602,7 @@ static int index_update(const orc_state* s, int x, int y, int z, const double G[
 }
 
 /* One time step: the phase-field scheme (Sec. 3.2) then the heat scheme
- * (Sec. 3.1), as the paper prescribes ("the heat equation must be solved after
- * solving the phase-field equation"). */
+ * (Sec. 3.1), in the order the paper prescribes (heat after phase field). */
 static void step_once(orc_state* s)
 {
     const orc_params* p = &s->p;
@@ -632,8 +631,9 @@ static void step_once(orc_state* s)
      *     - (g_i(x,t) - g_i^(0)(x,t)) / eta_phi + w_i Q_phi dt / tau0,
      * with eta_phi from Eq. (LBE_RelaxationTime) and Q_phi from
      * Eq. (LBE_SourceTerm).  Reading: a_s, N and eta_phi are those of the
-     * node x for every occurrence ("treated explicitly in time"), and the
-     * non-local g_i(x + e_i dx, t) is the population before streaming. */
+     * node x for every occurrence (the paper takes the non-local term
+     * explicit in time), and the non-local g_i(x + e_i dx, t) is the
+     * population before streaming. */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
