@@ -105,10 +105,9 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     constexpr int HL = XZV ? 0 : 2, HC = XZV ? 0 : 1;       // halo rows (y) of the phi and coefficient planes
     constexpr int RX = TXT + 4, RY = TY + 2 * HL, RP = RX * RY;  // tile + 2-site halo
     constexpr int CX = TXT + 2, CY = TY + 2 * HC, CP = CX * CY;  // tile + 1-site halo
-    // phi / index ring depth: planes z-1 .. z+3 in use while plane z is output;
-    // with deviation storage the output reads phi^n at z-1 while the next
-    // plane's copy (z+4) may already be issued, hence one more slot
-    constexpr int NPH = S::dev ? 6 : 5;
+    // phi / index ring depth: planes z-1 .. z+3 in use while plane z is output
+    // (the output phase reads phi^n only at its own plane)
+    constexpr int NPH = 5;
     constexpr int NH = 4;                                   // h ring depth (z .. z+3)
     constexpr int NC = 3;                                   // coefficient ring depth
     constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
@@ -389,7 +388,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             const R omp = (R(1) - ph) * (R(1) + ph);
             const R Qphi = (ph - lam * u * omp) * omp;
             const R vf = -De2 * ieta * iA2;
-            CoefIO<R>::store(dco, CP, ly * CX + lx, (R(1) - ieta) * iA2, iA2 - R(1), (ph * ieta + qphi * Qphi) * iA2,
+            // with deviation storage the source coefficient also carries
+            // c1 phi (x): c1 (w_i phi + d_i) + w_i s = c1 d_i + w_i (s + c1 phi),
+            // and s + c1 phi = (phi + (dt/tau0) Q_phi) / a_s^2
+            const R sc = DEV ? (ph + qphi * Qphi) * iA2 : (ph * ieta + qphi * Qphi) * iA2;
+            CoefIO<R>::store(dco, CP, ly * CX + lx, (R(1) - ieta) * iA2, iA2 - R(1), sc,
                              vf * Nx, vf * Ny, vf * Nz);
         }
     };
@@ -416,12 +419,12 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const int px = ltx + 2, py = lty + HL;  // phi frame
         const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
         R gl[QG];
+        R d0 = 0;
         if (!DEV) {
 #pragma unroll
             for (int i = 0; i < QG; ++i) gl[i] = to_real(gc[(long long)i * n + s]);
         } else {
             const R phy = s_phi[sphi(z) * RP + py * RX + px];
-            R d0 = 0;
 #pragma unroll
             for (int i = 1; i < QG; ++i) {
                 const R d = to_real(gc[(long long)(i - 1) * n + s]);
@@ -438,14 +441,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             R c1, c2, cs, vx, vy, vz;
             CoefIO<R>::load(s_co + sco(z - ez) * NCO * CP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
                             cs, vx, vy, vz);
-            R gp;
-            if (i == 0) {
-                gp = gl[0];
-            } else if (!DEV) {
-                gp = to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
+            R gp;  // full storage: g_i(x); deviation storage: d_i(x) (w_i phi(x) is in cs)
+            if (!DEV) {
+                gp = i == 0 ? gl[0] : to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
             } else {
-                const R phs = s_phi[sphi(z - ez) * RP + (py - ey) * RX + (px - ex)];
-                gp = R(PL::w(i)) * phs + to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
+                gp = i == 0 ? d0 : to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
             }
             R ev = R(0);
             if (ex) ev += R(ex) * vx;
@@ -530,7 +530,7 @@ constexpr size_t step_smem_bytes()
     using R = typename S::Real;
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
     constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
-    constexpr int NPH = S::dev ? 6 : 5, NH = 4, NC = 3, NCO = 6;
+    constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
     using T = typename S::T;
     constexpr size_t stf = IsXZ<PL>::value && sizeof(T) == 4 && !S::dev ? (size_t)UL::Q * RP * sizeof(T) : 0;
     return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) + stf;
