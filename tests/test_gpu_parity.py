@@ -235,6 +235,53 @@ def test_fp32_3d_vs_oracle(L, O):
     assert otip[0] > 9.0  # grew
 
 
+@pytest.mark.parametrize("grad", [0, 1])
+def test_fp32_2d_vs_oracle(L, O, grad):
+    """2D plain method in FP32 (the y-marched strips with the heat pull
+    sources staged in shared memory) against the FP64 oracle: the FP32 bar of
+    the 3D case, at 500 and 1000 steps."""
+    w = W.c1(128)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 0, w["shape"], w["params"], cr, seeds=w["seeds"], grad=grad)
+    s = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"], grad=grad, precision=L.LBPF_FP32)
+    for k in range(2):
+        o.step(500)
+        s.step(500)
+        phi, u = s.fields()
+        ophi, ou, _ = o.fields()
+        tip = s.measure(*w["centre"])[0]
+        otip = o.measure(*w["centre"])[0]
+        e = (maxabs(phi, ophi), maxabs(u, ou), np.abs(tip - otip).max())
+        print(f"2D FP32 vs FP64 oracle after {500 * (k + 1)} steps: phi {e[0]:.2e}, u {e[1]:.2e}, tips {e[2]:.2e}")
+        assert e[0] <= 1e-4 and e[1] <= 1e-4 and e[2] <= 0.5
+
+
+def test_fp16dev_2d_sanity(L, O):
+    """2D with FP16 deviation storage: finite, close to the FP64 oracle, and
+    conserving sum(u - phi/2) to the storage's rounding."""
+    w = W.c1(128)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 0, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 0, w["shape"], w["params"], cr, seeds=w["seeds"], precision=L.LBPF_FP32_FP16DEV)
+    _, _, c0 = s.measure(*w["centre"])
+    o.step(1000)
+    s.step(1000)
+    phi, u = s.fields()
+    ophi, ou, _ = o.fields()
+    tip, _, c1 = s.measure(*w["centre"])
+    otip = o.measure(*w["centre"])[0]
+    print(f"2D FP16 deviations vs FP64 oracle after 1000 steps: phi {maxabs(phi, ophi):.2e}, u {maxabs(u, ou):.2e}, "
+          f"tips {np.abs(tip - otip).max():.2e}")
+    assert np.isfinite(phi).all() and np.isfinite(u).all()
+    assert maxabs(phi, ophi) < 0.5 and np.abs(tip - otip).max() < 1.0
+    # The scheme conserves sum(u - phi/2) exactly; in FP32 every site rounds
+    # its update each step, and in the uniform bulk (most of this box) all
+    # sites round the same way, so the errors add up coherently instead of
+    # cancelling (the FP32 full-storage run drifts alike, FP64 by 1e-13).
+    # Bound: one FP32 ulp of |u - phi/2| <= 0.25 per site and step.
+    assert abs(c1 - c0) <= phi.size * 1000 * 2.0 ** -25
+
+
 DEV16_NAMES = {2: "FP16", 3: "BF16", 4: "FP16, stochastic rounding"}
 
 
