@@ -23,16 +23,22 @@
 //   v  = -D_phi N / (e^2 eta_phi a_s^2),   D_phi = (W0^2/tau0)(dt/dx^2),
 // which is Eq. (LBE_Eq_Phase) divided by a_s^2(x) with g^(0) of Eq.
 // (Feq_Phase), eta_phi of Eq. (LBE_RelaxationTime) and Q_phi of Eq.
-// (LBE_SourceTerm), all evaluated at the collision node x.
+// (LBE_SourceTerm), all evaluated at the collision node x.  With deviation
+// storage (g_i = w_i phi + d_i) the pulled c1 w_i phi(x) is folded into the
+// source coefficient, which is then stored as s + c1 phi = (phi + (dt/tau0)
+// Q_phi) / a_s^2.
 //
 // Tiling: a block owns a TXT x TY column of sites and marches along z over
 // [z0, z1), keeping rings of planes in shared memory: phi^n and
 // h = aux + phi^n / 2 on the tile plus a 2-site halo, and the collision
 // coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
 // is read from HBM once per launch except the halo rims, which neighbouring
-// blocks share through L2.  A 2D domain is run through the same march with
-// its y axis as the kernel's z axis (lattice XZ<>): the tile is one row of
-// TXT sites, without halo rows.
+// blocks share through L2.  Per plane z: wait for the copies of phi/aux
+// plane z+2 and form h there, issue the cp.async copies of plane z+3,
+// barrier, coefficients of plane z+1, barrier, output of plane z.  A 2D
+// domain is run through the same march with its y axis as the kernel's z
+// axis (lattice XZ<>): the tile is one row of TXT sites, without halo rows,
+// and the heat pull sources of the next row are staged by cp.async too.
 #pragma once
 
 #include "lbpf_internal.cuh"
