@@ -228,8 +228,9 @@ def run_reference(args):
     return 0
 
 
-def run_surrogate(args, size=1024, train_size=128, steps_total=4400):
+def run_surrogate(args, size=1024):
     K, M, kv, alpha = args.sur_k, args.sur_m, args.sur_kv, args.sur_alpha
+    train_size, steps_total = args.sur_train_size, args.sur_steps
     n_draws, traj = args.sur_draws, args.sur_traj
     """Surrogate + LB vs plain LB on one 2D domain of the batched
     configuration's distributions: same final time, tip velocity from the
@@ -320,6 +321,8 @@ def main():
     ap.add_argument("--sur-draws", type=int, default=16, help="training draws")
     ap.add_argument("--sur-traj", type=int, default=2000, help="LB steps per training trajectory")
     ap.add_argument("--sur-train", type=int, default=1500, help="Adam steps")
+    ap.add_argument("--sur-train-size", type=int, default=128, help="side of the training domains")
+    ap.add_argument("--sur-steps", type=int, default=4400, help="LB steps to solution of the timed run")
     ap.add_argument("--surrogate", action="store_true",
                     help="time-to-solution of surrogate + LB vs plain LB (trains a network first)")
     args = ap.parse_args()
