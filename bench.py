@@ -61,6 +61,23 @@ def peaks():
         return None
 
 
+def rank_max(x: float, dist=None, device="cuda") -> float:
+    """The largest x over all ranks (x itself without a process group): the
+    job's time is that of its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, sites: float, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica of `sites` sites
+    by `steps` steps; `seconds` is the max over ranks."""
+    return world * sites * steps / seconds / 1e6
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -377,12 +394,8 @@ def main():
         torch.cuda.synchronize()
     launches = int(s.query(L.LBPF_Q_STEP_KERNELS) - k0)
     per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])  # ms
-    total_ms = float(ev[0].elapsed_time(ev[-1]))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = rank_max(float(ev[0].elapsed_time(ev[-1])), dist)
+    value = job_rate(world, sites, args.steps, total_ms * 1e-3)
     tip, sf, cons = s.measure(*w["centre"])
 
     # end to end through the public API with host buffers: write the initial
@@ -403,13 +416,9 @@ def main():
         s.step(args.steps)
         L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_PHI, phi_h)
         L.lbpf_read_field(s.ctx, 0, L.LBPF_FIELD_U, u_h)
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = rank_max(time.perf_counter() - t0, dist)
         nb = phi_h.numel() * phi_h.element_size()
-        e2e = {"value": round(world * sites * args.steps / el / 1e6, 2), "unit": "MLUPS",
+        e2e = {"value": round(job_rate(world, sites, args.steps, el), 2), "unit": "MLUPS",
                "h2d_bytes_per_step": round(2 * nb / args.steps, 1), "d2h_bytes_per_step": round(2 * nb / args.steps, 1),
                "note": f"write_fields from pinned host + {args.steps} steps + read phi,u to pinned host"}
 
