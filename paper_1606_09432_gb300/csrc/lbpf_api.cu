@@ -198,12 +198,18 @@ static int set_schedule(lbpf_ctx* c, int v, int seg)
 static std::string tune_key(const lbpf_ctx* c)
 {
     char buf[160];
-    unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the domain sizes
+    // FNV-1a over the domain sizes and the build time of this library, so
+    // that a rebuilt kernel is timed again instead of taking a stale choice
+    unsigned long long h = 1469598103934665603ULL;
     for (const DomainDev& d : c->dd)
         for (int v : {d.nx, d.ny, d.nz, d.use_index}) {
             h ^= (unsigned long long)(unsigned)v;
             h *= 1099511628211ULL;
         }
+    for (const char* p = __DATE__ " " __TIME__; *p; ++p) {
+        h ^= (unsigned char)*p;
+        h *= 1099511628211ULL;
+    }
     snprintf(buf, sizeof(buf), "s2-lat%d-prec%d-grad%d-dom%d-%016llx-sm%d", c->lattice, c->precision, c->grad,
              c->n_domains, h, c->sms);
     return buf;
