@@ -453,6 +453,8 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "check": {"tip_x": round(float(tip[0]), 4), "solid_fraction": sf, "conserved": cons},
+        "step_ms": {"median": round(float(np.median(per)), 4), "min": round(float(per.min()), 4),
+                    "max": round(float(per.max()), 4), "note": "CUDA events around every step launch"},
         "schedule": {"tile_rows": s.query(L.LBPF_Q_TILE_ROWS), "segment": s.query(L.LBPF_Q_SEGMENT),
                      "blocks": s.query(L.LBPF_Q_BLOCKS)},
     }
