@@ -34,7 +34,8 @@
 // coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
 // is read from HBM once per launch except the halo rims, which neighbouring
 // blocks share through L2.  Per plane z: wait for the copies of phi/aux
-// plane z+2 and form h there, issue the cp.async copies of plane z+3,
+// plane z+2 and form h there, issue the cp.async copies of plane z+3 (in
+// 3D interior rows in 16-byte chunks that bypass L1, halo columns by element),
 // barrier, coefficients of plane z+1, barrier, output of plane z.  A 2D
 // domain is run through the same march with its y axis as the kernel's z
 // axis (lattice XZ<>): the tile is one row of TXT sites, without halo rows,
@@ -109,7 +110,12 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     constexpr int D = PL::D;
     constexpr bool XZV = IsXZ<PL>::value;                   // 2D domain, y marched as z
     constexpr int HL = XZV ? 0 : 2, HC = XZV ? 0 : 1;       // halo rows (y) of the phi and coefficient planes
-    constexpr int RX = TXT + 4, RY = TY + 2 * HL, RP = RX * RY;  // tile + 2-site halo
+    // phi frame: tile + 2-site halo; in 3D the tile starts XO elements (16
+    // bytes) into each row so that interior rows can be copied in 16-byte
+    // chunks (in 2D the chunked copy measured slower and is not used)
+    constexpr int XO = (XZV || sizeof(R) >= 8) ? 2 : 4;
+    constexpr bool CHUNKED = !XZV;
+    constexpr int RX = TXT + 2 * XO, RY = TY + 2 * HL, RP = RX * RY;
     constexpr int CX = TXT + 2, CY = TY + 2 * HC, CP = CX * CY;  // tile + 1-site halo
     // phi / index ring depth: planes z-1 .. z+3 in use while plane z is output
     // (the output phase reads phi^n only at its own plane)
@@ -192,16 +198,49 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         R* dh = s_h + sh(zp) * RP;
         int8_t* dI = s_I + sphi(zp) * RP;
         const int rows = th + 2 * HL;
-        for (int k = tid; k < RX * rows; k += NT) {
-            const int ly = k / RX, lx = k - ly * RX;
-            if (lx >= tw + 4) continue;
-            const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dphi + k)),
-                         "l"(phic + s), "n"((int)sizeof(R)));
-            if (need_h)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dh + k)),
-                             "l"(auxc + s), "n"((int)sizeof(R)));
-            if (use_index) dI[k] = Ic[s];
+        constexpr int EPC = 16 / (int)sizeof(R), NCH = TXT / EPC;
+        auto cp4 = [&](R* d, const R* g) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(d)), "l"(g),
+                         "n"((int)sizeof(R)));
+        };
+        auto cp16 = [&](R* d, const R* g) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(d)), "l"(g));
+        };
+        if (CHUNKED && tw == TXT && nx % EPC == 0) {
+            // full tile: interior rows in 16-byte chunks (L2 only), the four
+            // halo columns element by element
+            const int nint = rows * NCH, nall = nint + rows * 4;
+            for (int t = tid; t < nall; t += NT) {
+                if (t < nint) {
+                    const int ly = t / NCH, c = t - ly * NCH;
+                    const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + x0 + c * EPC;
+                    const int k = ly * RX + XO + c * EPC;
+                    cp16(dphi + k, phic + s);
+                    if (need_h) cp16(dh + k, auxc + s);
+                } else {
+                    const int u = t - nint, ly = u >> 2, q = u & 3;
+                    const int lx = q < 2 ? XO - 2 + q : XO + TXT + (q - 2);
+                    const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO);
+                    const int k = ly * RX + lx;
+                    cp4(dphi + k, phic + s);
+                    if (need_h) cp4(dh + k, auxc + s);
+                }
+            }
+            if (use_index)
+                for (int k = tid; k < RX * rows; k += NT) {
+                    const int ly = k / RX, lx = k - ly * RX;
+                    if (lx < XO - 2 || lx >= XO + tw + 2) continue;
+                    dI[k] = Ic[zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO)];
+                }
+        } else {
+            for (int k = tid; k < RX * rows; k += NT) {
+                const int ly = k / RX, lx = k - ly * RX;
+                if (lx < XO - 2 || lx >= XO + tw + 2) continue;
+                const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO);
+                cp4(dphi + k, phic + s);
+                if (need_h) cp4(dh + k, auxc + s);
+                if (use_index) dI[k] = Ic[s];
+            }
         }
         asm volatile("cp.async.commit_group;");
     };
@@ -211,9 +250,26 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const R* dphi = s_phi + sphi(zp) * RP;
         R* dh = s_h + sh(zp) * RP;
         const int rows = th + 2 * HL;
+        constexpr int EPC = 16 / (int)sizeof(R), NCH = TXT / EPC;
+        if (CHUNKED && tw == TXT && nx % EPC == 0) {  // the tasks of async_plane's chunked path
+            const int nint = rows * NCH, nall = nint + rows * 4;
+            for (int t = tid; t < nall; t += NT) {
+                if (t < nint) {
+                    const int ly = t / NCH, c = t - ly * NCH;
+                    const int k = ly * RX + XO + c * EPC;
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) dh[k + e] += R(0.5) * dphi[k + e];
+                } else {
+                    const int u = t - nint, ly = u >> 2, q = u & 3;
+                    const int k = ly * RX + (q < 2 ? XO - 2 + q : XO + TXT + (q - 2));
+                    dh[k] += R(0.5) * dphi[k];
+                }
+            }
+            return;
+        }
         for (int k = tid; k < RX * rows; k += NT) {
             const int ly = k / RX, lx = k - ly * RX;
-            if (lx >= tw + 4) continue;
+            if (lx < XO - 2 || lx >= XO + tw + 2) continue;
             dh[k] += R(0.5) * dphi[k];
         }
     };
@@ -228,8 +284,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const int rows = th + 2 * HL;
         for (int k = tid; k < RX * rows; k += NT) {
             const int ly = k / RX, lx = k - ly * RX;
-            if (lx >= tw + 4) continue;
-            const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
+            if (lx < XO - 2 || lx >= XO + tw + 2) continue;
+            const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO);
             const R ph = phic[s];
             dphi[k] = ph;
             if (need_h) dh[k] = auxc[s] + R(0.5) * ph;
@@ -246,8 +302,8 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const int rows = th + 2 * HL;
         for (int k = tid; k < RX * rows; k += NT) {
             const int ly = k / RX, lx = k - ly * RX;
-            if (lx >= tw + 4) continue;
-            const long long rowx = (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - 2);
+            if (lx < XO - 2 || lx >= XO + tw + 2) continue;
+            const long long rowx = (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO);
 #pragma unroll
             for (int j = 0; j < QU; ++j) {
                 const long long s = (long long)wrapz(zp - UL::ez(j)) * nxy + rowx;
@@ -269,7 +325,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         for (int k = tid; k < CX * rows; k += NT) {
             const int ly = k / CX, lx = k - ly * CX;
             if (lx >= tw + 2) continue;
-            const int px = lx + 1, py = ly + HL - HC;  // position in the phi frame
+            const int px = lx + XO - 1, py = ly + HL - HC;  // position in the phi frame
             const int gx = wrapx(x0 + lx - 1), gy = wrapy(y0 + ly - HC);
             const long long s = zo + (long long)gy * nx + gx;
             const bool inner = store && lx >= 1 && lx <= tw && ly >= HC && ly < th + HC;
@@ -422,7 +478,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             return (ex < 0 ? oxm : (ex > 0 ? oxp : 0)) + (ey < 0 ? oym : (ey > 0 ? oyp : 0)) +
                    (D == 3 ? (ez < 0 ? ozm : (ez > 0 ? ozp : 0)) : 0);
         };
-        const int px = ltx + 2, py = lty + HL;  // phi frame
+        const int px = ltx + XO, py = lty + HL;  // phi frame
         const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
         R gl[QG];
         R d0 = 0;
@@ -535,7 +591,8 @@ constexpr size_t step_smem_bytes()
 {
     using R = typename S::Real;
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
-    constexpr int RP = (TXT + 4) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
+    constexpr int XO = (IsXZ<PL>::value || sizeof(R) >= 8) ? 2 : 4;
+    constexpr int RP = (TXT + 2 * XO) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
     constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
     using T = typename S::T;
     constexpr size_t stf = IsXZ<PL>::value && sizeof(T) == 4 && !S::dev ? (size_t)UL::Q * RP * sizeof(T) : 0;
