@@ -33,7 +33,9 @@
 // h = aux + phi^n / 2 on the tile plus a 2-site halo, and the collision
 // coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
 // is read from HBM once per launch except the halo rims, which neighbouring
-// blocks share through L2.  Per plane z: wait for the copies of phi/aux
+// blocks share through L2.  A work item starts by loading planes z0-2 ..
+// z0+1 (asynchronously with full storage) and computing two coefficient
+// planes.  Then per plane z: wait for the copies of phi/aux
 // plane z+2 and form h there, issue the cp.async copies of plane z+3 (in
 // 3D interior rows in 16-byte chunks that bypass L1, halo columns by element),
 // barrier, coefficients of plane z+1, barrier, output of plane z.  A 2D
@@ -531,10 +533,15 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 
     {
         const int z0 = it.z0, z1 = it.z1;
-        load_plane(z0 - 2);
-        load_plane(z0 - 1);
-        load_plane(z0);
-        load_plane(z0 + 1);
+        if constexpr (!DEV) {  // prologue copies asynchronous too (+3 % FP32, -2 % deviations: measured)
+            for (int p = z0 - 2; p <= z0 + 1; ++p) async_plane(p);
+            for (int p = z0 - 2; p <= z0 + 1; ++p) finish_plane(p);
+        } else {
+            load_plane(z0 - 2);
+            load_plane(z0 - 1);
+            load_plane(z0);
+            load_plane(z0 + 1);
+        }
         __syncthreads();
         coef_plane(z0 - 1, false, false);
         coef_plane(z0, true, false);
