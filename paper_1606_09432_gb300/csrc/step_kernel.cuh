@@ -33,9 +33,7 @@
 // h = aux + phi^n / 2 on the tile plus a 2-site halo, and the collision
 // coefficients (c1, c2, s, v) on the tile plus a 1-site halo.  Every value
 // is read from HBM once per launch except the halo rims, which neighbouring
-// blocks share through L2.  A work item starts by loading planes z0-2 ..
-// z0+1 (asynchronously with full storage) and computing two coefficient
-// planes.  Then per plane z: wait for the copies of phi/aux
+// blocks share through L2.  Per plane z: wait for the copies of phi/aux
 // plane z+2 and form h there, issue the cp.async copies of plane z+3 (in
 // 3D interior rows in 16-byte chunks that bypass L1, halo columns by element),
 // barrier, coefficients of plane z+1, barrier, output of plane z.  A 2D
