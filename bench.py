@@ -190,6 +190,15 @@ def make_solver(L, W, workload, stream, size=0):
     return s, w
 
 
+def oracle_threads() -> int:
+    """Threads the OpenMP oracle runs with: OMP_NUM_THREADS when set, else
+    every host core."""
+    try:
+        return max(1, int(os.environ["OMP_NUM_THREADS"]))
+    except (KeyError, ValueError):
+        return os.cpu_count() or 1
+
+
 def cpu_oracle_rate(workload: str, budget_s: float, n: int = 64, max_steps: int | None = None):
     """Oracle MLUPS on a periodic n^3 crop of the workload (host cores)."""
     from oracle import oracle as O
@@ -231,7 +240,7 @@ def run_reference(args):
     o.step(args.steps)
     el = time.perf_counter() - t0
     v = n ** 3 * args.steps / el / 1e6
-    cores = os.cpu_count()
+    cores = oracle_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
@@ -436,7 +445,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1 and not args.workload.startswith("c4"):
         v, st, el = cpu_oracle_rate(args.workload, args.cpu_budget, n=96)
-        cpu = {"value": round(v, 3), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": round(v, 3), "unit": "MLUPS", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"96^3 periodic crop of the workload, {st} FP64 oracle steps in {el:.1f} s"}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
