@@ -16,6 +16,10 @@
 // whose kernels overlap on the GPU (different streams, or different host
 // threads on one device) race on the array and must be serialised by the
 // caller.
+//
+// The device address of the array is looked up once per device (the first
+// call on that device) and cached; a cudaDeviceReset destroys the context
+// that address belongs to, so calls after a device reset are not supported.
 #include <cmath>
 #include <mutex>
 
@@ -79,12 +83,28 @@ __global__ void __launch_bounds__(kStaticBlockThreads)
     }
 }
 
-__global__ void static_sums_finish_kernel(const double* partial, int nblocks, double* out)
+// Sums the per-block partials in a fixed order (thread t takes blocks t,
+// t + 256, ...; then a fixed tree over the threads), so results are
+// deterministic run to run.
+__global__ void __launch_bounds__(kStaticBlockThreads)
+    static_sums_finish_kernel(const double* partial, int nblocks, double* out)
 {
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += kStaticBlockThreads)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t[k] += partial[3 * b + k];
+    __shared__ double red[3][kStaticBlockThreads / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = warp_sum_static(t[k]);
+        if (l == 0) red[k][w] = v;
+    }
+    __syncthreads();
     if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int b = 0; b < nblocks; ++b) t += partial[3 * b + threadIdx.x];
-        out[threadIdx.x] = t;
+        double v = 0.0;
+        for (int j = 0; j < kStaticBlockThreads / 32; ++j) v += red[threadIdx.x][j];
+        out[threadIdx.x] = v;
     }
 }
 
@@ -116,12 +136,23 @@ extern "C" int lbpf_field_sums_static(const void* phi, const void* u, long long 
     }
     const int blocks = (int)((n + kStaticChunk - 1) / kStaticChunk);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // An error pending before this call belongs to the caller: it is neither
+    // reported as ours nor cleared.  A launch error of our own kernels is
+    // cleared and reported as LBPF_ECUDA.
+    const cudaError_t before = cudaPeekAtLastError();
     if (precision == LBPF_FP64)
         static_sums_kernel<double><<<blocks, kStaticBlockThreads, 0, s>>>(static_cast<const double*>(phi),
                                                                            static_cast<const double*>(u), n, partials);
     else
         static_sums_kernel<float><<<blocks, kStaticBlockThreads, 0, s>>>(static_cast<const float*>(phi),
                                                                           static_cast<const float*>(u), n, partials);
-    static_sums_finish_kernel<<<1, 32, 0, s>>>(partials, blocks, out);
-    return cudaGetLastError() == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
+    cudaError_t e = cudaPeekAtLastError();
+    if (e == cudaSuccess || e == before)
+        static_sums_finish_kernel<<<1, kStaticBlockThreads, 0, s>>>(partials, blocks, out);
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess && e != before) {
+        cudaGetLastError();
+        return LBPF_ECUDA;
+    }
+    return LBPF_OK;
 }
