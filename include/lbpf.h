@@ -186,12 +186,45 @@ int lbpf_step(lbpf_ctx* ctx, int n_steps);
 typedef enum {
     LBPF_FIELD_PHI = 0,   /* phi, Eq. (Def_M0_Phi)                          */
     LBPF_FIELD_U = 1,     /* u, Eq. (Temperature_LB)                        */
-    LBPF_FIELD_INDEX = 2  /* crystal index I (int32), Sec. 4.3; all 1 with one crystal */
+    LBPF_FIELD_INDEX = 2, /* crystal index I (int32), Sec. 4.3; all 1 with one crystal */
+    LBPF_FIELD_AS = 3     /* a_s(n) of the current phi (see lbpf_read_fields) */
 } lbpf_field;
 
-/* Copy one field of one domain to out (device memory of the context's GPU if
- * out_on_device != 0, else host memory).  out_bytes must be at least
- * nx*ny*nz * element size.  Synchronises the stream.
+/* Field selection bits of lbpf_read_fields.  The selected fields are written
+ * back to back in increasing bit order, each nx*ny*nz elements: phi, u and
+ * a_s in the arithmetic type (double for LBPF_FP64, float otherwise), then
+ * the index field as int32 (last, so that every double stays 8-byte
+ * aligned when out is). */
+#define LBPF_READ_PHI   (1u << 0)
+#define LBPF_READ_U     (1u << 1)
+#define LBPF_READ_AS    (1u << 2)
+#define LBPF_READ_INDEX (1u << 3)
+
+/* Copy the fields selected by mask (LBPF_READ_* bits, at least one) of one
+ * domain into out, in the order and types given above:
+ *   phi: Eq. (Def_M0_Phi), the zeroth moment of the phase-field populations;
+ *   u:   Eq. (Temperature_LB), the zeroth moment of the heat populations (a
+ *        lagged heat update is brought up to date first);
+ *   a_s: the anisotropy function of the site's crystal, Eqs.
+ *        (As_Function_Classical), (As_Theta), (As_Y66), (As_MatSci),
+ *        (As_Function_S), at the normal n = -grad phi / |grad phi| of Eq.
+ *        (Def_Normal_Vector) of the current phi, with the context's gradient
+ *        operator (Sec. 4.2); 1 where the crystal index is 0 or |grad phi|
+ *        is below the zero-gradient guard (1e-10 lattice units in FP64, 1e-6
+ *        in FP32).  Evaluated on the device by the same code as the step;
+ *   index: the crystal index field of Sec. 4.3 (1 everywhere with one crystal).
+ * out is device memory of the context's GPU if out_on_device != 0, else host
+ * memory (pinned memory makes the copies asynchronous DMA); the caller owns
+ * it.  out_bytes must cover every selected field.  The library allocates no
+ * memory: host reads are staged through a device buffer the context owns.
+ * Synchronises the stream once, at the end.
+ * Errors: LBPF_EINVAL (bad domain, NULL out, empty or unknown mask bits),
+ * LBPF_ERANGE (buffer too small), LBPF_ECUDA. */
+int lbpf_read_fields(lbpf_ctx* ctx, int domain, unsigned mask, void* out, int out_on_device, size_t out_bytes);
+
+/* One field of one domain (field: lbpf_field); the same as lbpf_read_fields
+ * with the one matching bit.  out_bytes must be at least nx*ny*nz * element
+ * size.  Synchronises the stream.
  * Errors: LBPF_ERANGE (buffer too small), LBPF_EINVAL, LBPF_ECUDA. */
 int lbpf_read_field(lbpf_ctx* ctx, int domain, int field, void* out, int out_on_device,
                     size_t out_bytes);
@@ -201,7 +234,8 @@ int lbpf_read_field(lbpf_ctx* ctx, int domain, int field, void* out, int out_on_
  * Q_phi arrays of nx*ny*nz), which = 1 for f_i (temperature, Q_u arrays).
  * Population i of site k is at [i * nx*ny*nz + k]; direction numbering as in
  * Sec. 3.3 (D3Q19/D3Q27: axes, then the xy-, xz-, yz-edges, then corners).
- * Synchronises the stream. */
+ * Host reads are staged through a device buffer the context owns (no
+ * allocation per call).  Synchronises the stream. */
 int lbpf_read_populations(lbpf_ctx* ctx, int domain, int which, void* out, int out_on_device,
                           size_t out_bytes);
 

@@ -721,10 +721,29 @@ int orc_get_populations(const orc_state* s, double* g, double* f)
     return 0;
 }
 
-/* a_s at every site (for the anisotropy-field pictures of Sec. 4). */
+/* a_s at every site as used by the last step (computed from the phase
+ * field before that step). */
 int orc_get_anisotropy(const orc_state* s, double* a)
 {
     memcpy(a, s->a, sizeof(double) * s->n);
+    return 0;
+}
+
+/* a_s at every site of the current phase field (the anisotropy-field
+ * pictures of Sec. 4): the normal of Eq. (Def_Normal_Vector) from the
+ * gradient of the current phi (Sec. 4.2) and the a_s of the site's crystal
+ * for the current index field; a_s = 1 where the index is 0. */
+int orc_anisotropy_field(const orc_state* s, double* a)
+{
+    const orc_params* p = &s->p;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = site(p, x, y, z);
+                double G[3], N[3];
+                gradient_at(p, &s->Lg, s->phi, x, y, z, G);
+                site_anisotropy(s, s->I[k], G, &a[k], N);
+            }
     return 0;
 }
 

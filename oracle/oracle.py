@@ -96,6 +96,7 @@ def lib():
         _lib.orc_get_fields.argtypes = [C.c_void_p, d, d, i]
         _lib.orc_get_populations.argtypes = [C.c_void_p, d, d]
         _lib.orc_get_anisotropy.argtypes = [C.c_void_p, d]
+        _lib.orc_anisotropy_field.argtypes = [C.c_void_p, d]
         _lib.orc_measure.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, d, d, d]
         _lib.orc_lattice.argtypes = [C.c_int, C.c_int, i, i, i, d, d]
         _lib.orc_gradient.argtypes = [C.POINTER(Params), d, d]
@@ -229,8 +230,15 @@ class Oracle:
         return g, f
 
     def anisotropy_field(self):
+        """a_s used by the last step (from the phase field before it)."""
         a = np.zeros(self.shape)
         lib().orc_get_anisotropy(self._h, _dp(a))
+        return a
+
+    def current_anisotropy(self):
+        """a_s of the current phase field and index field."""
+        a = np.zeros(self.shape)
+        lib().orc_anisotropy_field(self._h, _dp(a))
         return a
 
     def measure(self, cx: int, cy: int, cz: int = 0):

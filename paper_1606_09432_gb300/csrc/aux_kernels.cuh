@@ -187,9 +187,10 @@ __global__ void read_u_kernel(const DomainDev* dp, int cur, int fcur, int acur, 
     }
 }
 
-// Decoded populations of a synchronised state.
+// Decoded population i of a synchronised state (which = 0: g_i, 1: f_i).
 template <class PL, class UL, class S>
-__global__ void read_pops_kernel(const DomainDev* dp, int which, int cur, int fcur, int acur, typename S::Real* out)
+__global__ void read_pop_kernel(const DomainDev* dp, int which, int i, int cur, int fcur, int acur,
+                                typename S::Real* out)
 {
     using R = typename S::Real;
     using T = typename S::T;
@@ -201,18 +202,43 @@ __global__ void read_pops_kernel(const DomainDev* dp, int which, int cur, int fc
     const R* aux = static_cast<const R*>(d.aux[acur]);
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         if (!S::dev) {
-            for (int i = 0; i < Q; ++i) out[(long long)i * n + s] = to_real(p[(long long)i * n + s]);
+            out[s] = to_real(p[(long long)i * n + s]);
         } else {
             const R m = which == 0 ? phi[s] : aux[s] + R(0.5) * phi[s];
-            R d0 = 0;
-            for (int i = 1; i < Q; ++i) {
-                const R dv = to_real(p[(long long)(i - 1) * n + s]);
+            if (i > 0) {
                 const R wi = which == 0 ? R(PL::w(i)) : R(UL::w(i));
-                out[(long long)i * n + s] = wi * m + dv;
-                d0 -= dv;
+                out[s] = wi * m + to_real(p[(long long)(i - 1) * n + s]);
+            } else {
+                R d0 = 0;
+                for (int j = 1; j < Q; ++j) d0 -= to_real(p[(long long)(j - 1) * n + s]);
+                out[s] = (which == 0 ? R(PL::w(0)) : R(UL::w(0))) * m + d0;
             }
-            out[s] = (which == 0 ? R(PL::w(0)) : R(UL::w(0))) * m + d0;
         }
+    }
+}
+
+// a_s(n) of the current phase field, n = -grad(phi)/|grad(phi)| (Eq.
+// Def_Normal_Vector) with the gradient operator of the context, evaluated by
+// the step kernel's anisotropy(); the crystal is the current index (one
+// crystal: everywhere), a_s = 1 where the index is 0.
+template <class PL, class S>
+__global__ void read_as_kernel(const DomainDev* dp, int cur, int grad, typename S::Real* out)
+{
+    using R = typename S::Real;
+    const DomainDev& d = *dp;
+    const R* phi = static_cast<const R*>(d.phi[cur]);
+    const int8_t* I = d.I[cur];
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < d.n; s += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        const SiteNb nb = site_nb(d, s, x, y, z);
+        const int cryst = d.use_index ? (int)I[s] : 1;
+        R a = 1, Nx, Ny, Nz;
+        if (cryst > 0 && cryst <= d.n_crystals) {
+            R Gx, Gy, Gz;
+            site_gradient<PL, R>(phi, s, nb, grad, Gx, Gy, Gz);
+            anisotropy<R, PL::D>(d.cr[cryst - 1], Gx, Gy, Gz, a, Nx, Ny, Nz);
+        }
+        out[s] = a;
     }
 }
 
@@ -277,15 +303,21 @@ struct LauncherImpl {
         read_u_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, cur, fcur, acur, static_cast<typename S::Real*>(out));
         return cudaGetLastError();
     }
-    static cudaError_t read_pops(const DomainDev* d, int which, int cur, int fcur, int acur, void* out, cudaStream_t s)
+    static cudaError_t read_pop(const DomainDev* d, int which, int i, int cur, int fcur, int acur, void* out,
+                                cudaStream_t s)
     {
-        read_pops_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, which, cur, fcur, acur,
-                                                            static_cast<typename S::Real*>(out));
+        read_pop_kernel<PL, UL, S><<<152 * 8, 256, 0, s>>>(d, which, i, cur, fcur, acur,
+                                                           static_cast<typename S::Real*>(out));
+        return cudaGetLastError();
+    }
+    static cudaError_t read_as(const DomainDev* d, int cur, int grad, void* out, cudaStream_t s)
+    {
+        read_as_kernel<PL, S><<<152 * 8, 256, 0, s>>>(d, cur, grad, static_cast<typename S::Real*>(out));
         return cudaGetLastError();
     }
     static const Launchers* get()
     {
-        static const Launchers L = {&step, &smem, &prepare, &blocks_per_sm, &heat_sync, &equilibrate, &read_u, &read_pops, PL::Q, UL::Q, PL::D};
+        static const Launchers L = {&step, &smem, &prepare, &blocks_per_sm, &heat_sync, &equilibrate, &read_u, &read_pop, &read_as, PL::Q, UL::Q, PL::D};
         return &L;
     }
 };

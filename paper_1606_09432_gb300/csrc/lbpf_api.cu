@@ -640,43 +640,62 @@ extern "C" int lbpf_step(lbpf_ctx* c, int n_steps)
     return LBPF_OK;
 }
 
-extern "C" int lbpf_read_field(lbpf_ctx* c, int domain, int field, void* out, int out_on_device, size_t out_bytes)
+// Element size of a field selected by one LBPF_READ_* bit.
+static size_t field_esize(const lbpf_ctx* c, unsigned bit) { return bit == LBPF_READ_INDEX ? sizeof(int) : c->rsize; }
+
+extern "C" int lbpf_read_fields(lbpf_ctx* c, int domain, unsigned mask, void* out, int out_on_device, size_t out_bytes)
 {
     int rc = check_ctx(c, domain);
     if (rc) return rc;
-    if (!out) return fail(c, LBPF_EINVAL, "lbpf_read_field: out is NULL");
+    constexpr unsigned kAll = LBPF_READ_PHI | LBPF_READ_U | LBPF_READ_AS | LBPF_READ_INDEX;
+    if (!out) return fail(c, LBPF_EINVAL, "lbpf_read_fields: out is NULL");
+    if (mask == 0 || (mask & ~kAll)) return fail(c, LBPF_EINVAL, "lbpf_read_fields: bad mask 0x%x", mask);
     const DomainDev& h = c->dd[domain];
-    const size_t esize = field == LBPF_FIELD_INDEX ? sizeof(int) : c->rsize;
-    const size_t bytes = (size_t)h.n * esize;
-    if (field < LBPF_FIELD_PHI || field > LBPF_FIELD_INDEX) return fail(c, LBPF_EINVAL, "lbpf_read_field: bad field %d", field);
-    if (out_bytes < bytes) return fail(c, LBPF_ERANGE, "lbpf_read_field: need %zu bytes, got %zu", bytes, out_bytes);
-    void* dst = out_on_device ? out : c->scratch;
-    if (field == LBPF_FIELD_PHI) {
-        CK(cudaMemcpyAsync(out, h.phi[c->cur], bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                           c->stream));
-    } else {
-        if (field == LBPF_FIELD_U) {
-            if ((rc = sync_state(c))) return rc;
-            CK(c->L->read_u(c->d_dd + domain, c->cur, c->fcur, c->acur, dst, c->stream));
-        } else if (h.use_index) {
-            CK(launch_index_to_i32(h.I[c->cur], static_cast<int*>(dst), h.n, c->stream));
-        } else {
-            // one crystal: index 1 everywhere (staged through the int8 view of scratch)
-            int8_t* tmp = static_cast<int8_t*>(c->scratch) + (size_t)h.n * 3;
-            if (out_on_device) {
-                CK(launch_fill_i8(tmp, 1, h.n, c->stream));
-                CK(launch_index_to_i32(tmp, static_cast<int*>(dst), h.n, c->stream));
-            } else {
-                CK(cudaStreamSynchronize(c->stream));
-                int* o = static_cast<int*>(out);
-                for (long long s = 0; s < h.n; ++s) o[s] = 1;
-                return LBPF_OK;
-            }
+    size_t need = 0;
+    for (unsigned bit = 1; bit <= LBPF_READ_INDEX; bit <<= 1)
+        if (mask & bit) need += (size_t)h.n * field_esize(c, bit);
+    if (out_bytes < need) return fail(c, LBPF_ERANGE, "lbpf_read_fields: need %zu bytes, got %zu", need, out_bytes);
+    if (mask & LBPF_READ_U)
+        if ((rc = sync_state(c))) return rc;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char* o = static_cast<char*>(out);
+    for (unsigned bit = 1; bit <= LBPF_READ_INDEX; bit <<= 1) {
+        if (!(mask & bit)) continue;
+        const size_t bytes = (size_t)h.n * field_esize(c, bit);
+        // fields that need a kernel are written in place (device output) or
+        // into the context's scratch and copied from there (host output); the
+        // copies run in stream order, so the scratch is free again for the
+        // next field without a synchronisation
+        void* dst = out_on_device ? static_cast<void*>(o) : c->scratch;
+        switch (bit) {
+        case LBPF_READ_PHI:
+            CK(cudaMemcpyAsync(o, h.phi[c->cur], bytes, kind, c->stream));
+            dst = nullptr;
+            break;
+        case LBPF_READ_U: CK(c->L->read_u(c->d_dd + domain, c->cur, c->fcur, c->acur, dst, c->stream)); break;
+        case LBPF_READ_AS: CK(c->L->read_as(c->d_dd + domain, c->cur, c->grad, dst, c->stream)); break;
+        case LBPF_READ_INDEX:
+            if (h.use_index)
+                CK(launch_index_to_i32(h.I[c->cur], static_cast<int*>(dst), h.n, c->stream));
+            else
+                CK(launch_fill_i32(static_cast<int*>(dst), 1, h.n, c->stream));
+            break;
         }
-        if (!out_on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        if (dst && !out_on_device) CK(cudaMemcpyAsync(o, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        o += bytes;
     }
     CK(cudaStreamSynchronize(c->stream));
     return LBPF_OK;
+}
+
+extern "C" int lbpf_read_field(lbpf_ctx* c, int domain, int field, void* out, int out_on_device, size_t out_bytes)
+{
+    static const unsigned bits[4] = {LBPF_READ_PHI, LBPF_READ_U, LBPF_READ_INDEX, LBPF_READ_AS};
+    if (field < LBPF_FIELD_PHI || field > LBPF_FIELD_AS) {
+        int rc = check_ctx(c, domain);
+        return rc ? rc : fail(c, LBPF_EINVAL, "lbpf_read_field: bad field %d", field);
+    }
+    return lbpf_read_fields(c, domain, bits[field], out, out_on_device, out_bytes);
 }
 
 extern "C" int lbpf_read_populations(lbpf_ctx* c, int domain, int which, void* out, int out_on_device, size_t out_bytes)
@@ -686,16 +705,17 @@ extern "C" int lbpf_read_populations(lbpf_ctx* c, int domain, int which, void* o
     if (!out || (which != 0 && which != 1)) return fail(c, LBPF_EINVAL, "lbpf_read_populations: bad arguments");
     const DomainDev& h = c->dd[domain];
     const int Q = which == 0 ? c->Qg : c->Qu;
-    const size_t bytes = (size_t)Q * h.n * c->rsize;
+    const size_t bytes = (size_t)Q * h.n * c->rsize, one = (size_t)h.n * c->rsize;
     if (out_bytes < bytes) return fail(c, LBPF_ERANGE, "lbpf_read_populations: need %zu bytes, got %zu", bytes, out_bytes);
     if ((rc = sync_state(c))) return rc;
-    void* dst = out;
-    if (!out_on_device) CK(cudaMalloc(&dst, bytes));
-    cudaError_t e = c->L->read_pops(c->d_dd + domain, which, c->cur, c->fcur, c->acur, dst, c->stream);
-    if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (!out_on_device) cudaFree(dst);
-    if (e != cudaSuccess) return fail(c, LBPF_ECUDA, "lbpf_read_populations: %s", cudaGetErrorString(e));
+    // one population at a time, host reads through the context's scratch
+    for (int i = 0; i < Q; ++i) {
+        char* o = static_cast<char*>(out) + (size_t)i * one;
+        void* dst = out_on_device ? static_cast<void*>(o) : c->scratch;
+        CK(c->L->read_pop(c->d_dd + domain, which, i, c->cur, c->fcur, c->acur, dst, c->stream));
+        if (!out_on_device) CK(cudaMemcpyAsync(o, dst, one, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
     return LBPF_OK;
 }
 

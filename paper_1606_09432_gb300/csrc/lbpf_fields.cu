@@ -188,6 +188,10 @@ __global__ void fill_i8_kernel(int8_t* out, int8_t v, long long n)
 {
     for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) out[s] = v;
 }
+__global__ void fill_i32_kernel(int* out, int v, long long n)
+{
+    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) out[s] = v;
+}
 
 static int blocks_for(long long n)
 {
@@ -208,6 +212,11 @@ cudaError_t launch_index_from_i32(const int* in, int8_t* out, long long n, int n
 cudaError_t launch_fill_i8(int8_t* out, int8_t v, long long n, cudaStream_t s)
 {
     fill_i8_kernel<<<blocks_for(n), 256, 0, s>>>(out, v, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_i32(int* out, int v, long long n, cudaStream_t s)
+{
+    fill_i32_kernel<<<blocks_for(n), 256, 0, s>>>(out, v, n);
     return cudaGetLastError();
 }
 

@@ -381,8 +381,12 @@ struct Launchers {
                                cudaStream_t s);
     // u of a synced state into out (arithmetic type).
     cudaError_t (*read_u)(const DomainDev* d, int cur, int fcur, int acur, void* out, cudaStream_t s);
-    // Decoded populations (which = 0: g, 1: f) of a synced state into out.
-    cudaError_t (*read_pops)(const DomainDev* d, int which, int cur, int fcur, int acur, void* out, cudaStream_t s);
+    // Decoded population i (which = 0: g_i, 1: f_i) of a synced state into out.
+    cudaError_t (*read_pop)(const DomainDev* d, int which, int i, int cur, int fcur, int acur, void* out,
+                            cudaStream_t s);
+    // a_s(n) at every site from phi[cur] and the index field I[cur] (1 where
+    // |grad phi| is below the zero-gradient guard or the index is 0).
+    cudaError_t (*read_as)(const DomainDev* d, int cur, int grad, void* out, cudaStream_t s);
     int Qphi, Qu, D;
 };
 
@@ -417,5 +421,6 @@ cudaError_t launch_tip_radius(const void* phi, int nx, int ny, int nz, int cx, i
 cudaError_t launch_index_to_i32(const int8_t* in, int* out, long long n, cudaStream_t s);
 cudaError_t launch_index_from_i32(const int* in, int8_t* out, long long n, int n_crystals, cudaStream_t s);
 cudaError_t launch_fill_i8(int8_t* out, int8_t v, long long n, cudaStream_t s);
+cudaError_t launch_fill_i32(int* out, int v, long long n, cudaStream_t s);
 
 }  // namespace lbpf

@@ -21,11 +21,12 @@ LBPF_D2Q9_D2Q5, LBPF_D3Q15_D3Q7, LBPF_D3Q19_D3Q7, LBPF_D3Q27_D3Q7 = 0, 1, 2, 3
 LBPF_GRAD_DD, LBPF_GRAD_FD = 0, 1
 LBPF_FP64, LBPF_FP32, LBPF_FP32_FP16DEV, LBPF_FP32_BF16DEV, LBPF_FP32_FP16DEV_SR = range(5)
 LBPF_AS_CUBIC100, LBPF_AS_ANGLE, LBPF_AS_Y66, LBPF_AS_HOYT110, LBPF_AS_S111 = 0, 1, 2, 3, 4
-LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX = 0, 1, 2
+LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX, LBPF_FIELD_AS = 0, 1, 2, 3
+LBPF_READ_PHI, LBPF_READ_U, LBPF_READ_AS, LBPF_READ_INDEX = 1, 2, 4, 8
 (LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS,
  LBPF_Q_TILE_ROWS, LBPF_Q_SEGMENT, LBPF_Q_BLOCKS) = range(9)
 LBPF_MAX_CRYSTALS = 16
-EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_field",
+EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_fields", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
             "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius",
             "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
@@ -71,6 +72,7 @@ def load(path: str = LIB_PATH):
     lib.lbpf_seed.argtypes = [vp, C.c_int, C.POINTER(lbpf_seed_t), C.c_int]
     lib.lbpf_write_fields.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     lib.lbpf_step.argtypes = [vp, C.c_int]
+    lib.lbpf_read_fields.argtypes = [vp, C.c_int, C.c_uint, vp, C.c_int, C.c_size_t]
     lib.lbpf_read_field.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_size_t]
     lib.lbpf_read_populations.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_size_t]
     d = C.POINTER(C.c_double)
@@ -173,6 +175,16 @@ def lbpf_write_fields(ctx, domain, phi, u, index=None):
 
 def lbpf_step(ctx, n_steps=1):
     _check(load().lbpf_step(ctx, int(n_steps)), ctx)
+
+
+def lbpf_read_fields(ctx, domain, mask, out):
+    """Fields selected by mask (LBPF_READ_* bits) into out, back to back in
+    bit order (phi, u, a_s in the arithmetic type, then int32 index); out is a
+    host array or device tensor of enough bytes."""
+    p, dev = _ptr(out)
+    nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+    _check(load().lbpf_read_fields(ctx, domain, mask, p, dev, nbytes), ctx)
+    return out
 
 
 def lbpf_read_field(ctx, domain, field, out):
@@ -280,7 +292,15 @@ class Solver:
         return lbpf_read_field(self.ctx, domain, which, out)
 
     def fields(self, domain=0):
-        return self.field(LBPF_FIELD_PHI, domain), self.field(LBPF_FIELD_U, domain)
+        """(phi, u) read by one lbpf_read_fields call."""
+        shp = self.shape(domain)
+        out = np.empty((2,) + shp, dtype=self.dtype)
+        lbpf_read_fields(self.ctx, domain, LBPF_READ_PHI | LBPF_READ_U, out)
+        return out[0], out[1]
+
+    def anisotropy_field(self, domain=0):
+        """a_s of the current phi at every site (LBPF_FIELD_AS)."""
+        return self.field(LBPF_FIELD_AS, domain)
 
     def populations(self, which, domain=0):
         out = np.empty((self.Q[self.lattice][which],) + self.shape(domain), dtype=self.dtype)

@@ -457,3 +457,78 @@ def test_reduced_precision_tip_kinetics(L, O):
               f"tip radius {r:.3f} l.u. (oracle {orad:.3f}, rel err {er:.2e})")
         assert ev <= bv and er <= br
         s.close()
+
+
+@pytest.mark.parametrize("case", ["3d-hoyt", "2d-multi"])
+def test_read_fields_mask(L, O, case):
+    """lbpf_read_fields: phi, u, a_s and the index field in one call, into
+    host and device memory, against the oracle (a_s: the oracle's a_s of its
+    current phi and index field), plus a subset of the bits."""
+    import torch
+
+    if case == "3d-hoyt":
+        lattice, shape, prm = 1, (18, 21, 37), C2P
+        crs = [dict(kind=3, eps=0.02, gamma=-0.02)]
+        seeds = [(18.5, 10.2, 8.7, 5.0, 0)]
+        xi, steps = 1e-7, 40
+    else:
+        lattice, shape, prm = 0, (1, 50, 70), dict(W.C4_PARAMS, delta=0.35)
+        crs = [dict(kind=1, eps=0.04, q=4, phi0=0.785), dict(kind=1, eps=0.04, q=5, phi0=0.087),
+               dict(kind=1, eps=0.04, q=6, phi0=0.0)]
+        seeds = [(15.0, 14.0, 0, 5.0, 0), (50.0, 18.0, 0, 6.0, 1), (35.0, 38.0, 0, 4.5, 2)]
+        xi, steps = 1e-1, 120
+    o = oracle_run(O, lattice, shape, prm, crs, seeds=seeds, xi=xi)
+    s = gpu_run(L, lattice, shape, prm, crs, seeds=seeds, xi=xi)
+    o.step(steps)
+    s.step(steps)
+    ophi, ou, oI = o.fields()
+    oa = o.current_anisotropy()
+    n = int(np.prod(shape))
+    allbits = L.LBPF_READ_PHI | L.LBPF_READ_U | L.LBPF_READ_AS | L.LBPF_READ_INDEX
+    host = np.empty(3 * n * 8 + 4 * n, dtype=np.uint8)
+    L.lbpf_read_fields(s.ctx, 0, allbits, host)
+    dev = torch.empty(3 * n * 8 + 4 * n, dtype=torch.uint8, device="cuda")
+    L.lbpf_read_fields(s.ctx, 0, allbits, dev)
+    assert np.array_equal(dev.cpu().numpy(), host)
+    f = host[:3 * n * 8].view(np.float64).reshape((3,) + shape)
+    I = host[3 * n * 8:].view(np.int32).reshape(shape)
+    assert maxabs(f[0], ophi) <= 1e-10 and maxabs(f[1], ou) <= 1e-10
+    # a_s depends on the direction of grad phi, so a rounding difference
+    # delta in phi moves it by about delta / |grad phi|: the bar scales with
+    # 1 / |G| (G in lattice units); sites near the zero-gradient guard
+    # (1e-10) are left out
+    G = np.linalg.norm(O.gradient(o.p, ophi), axis=-1) * prm["dx"]
+    far = G > 1e-8
+    assert np.all(np.abs(f[2] - oa)[far] <= 1e-13 * (1.0 + 1.0 / G[far]))
+    print(f"a_s vs oracle: max {maxabs(f[2], oa):.2e}, where |G| > 1e-3: {maxabs(f[2][G > 1e-3], oa[G > 1e-3]):.2e}")
+    assert np.array_equal(I, oI)
+    assert np.abs(oa - 1.0).max() > 0.01  # the a_s field is not trivial
+    # a subset keeps the bit order: u, then the index field
+    sub = np.empty(n * 8 + n * 4, dtype=np.uint8)
+    L.lbpf_read_fields(s.ctx, 0, L.LBPF_READ_U | L.LBPF_READ_INDEX, sub)
+    assert np.array_equal(sub[:n * 8].view(np.float64).reshape(shape), f[1])
+    assert np.array_equal(sub[n * 8:].view(np.int32).reshape(shape), I)
+    assert np.array_equal(s.anisotropy_field(), f[2])
+    for mask in (0, 16):
+        with pytest.raises(L.LbpfError) as e:
+            L.lbpf_read_fields(s.ctx, 0, mask, host)
+        assert e.value.code == L.LBPF_EINVAL
+    with pytest.raises(L.LbpfError) as e:
+        L.lbpf_read_fields(s.ctx, 0, allbits, host[:-1])
+    assert e.value.code == L.LBPF_ERANGE
+
+
+def test_read_fields_fp32_as(L, O):
+    """a_s read back in FP32 against the oracle's a_s of its own phi."""
+    w = W.c3(40, eps=0.02, gamma=-0.02)
+    cr = [w["aniso"]]
+    o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
+    s = gpu_run(L, 1, w["shape"], w["params"], cr, seeds=w["seeds"], precision=L.LBPF_FP32)
+    o.step(100)
+    s.step(100)
+    a = s.anisotropy_field()
+    oa = o.current_anisotropy()
+    G = np.linalg.norm(O.gradient(o.p, o.fields()[0]), axis=-1) * w["params"]["dx"]
+    far = G > 1e-2  # the interface; FP32 rounding of phi moves a_s by ~1e-7 / |G|
+    print(f"FP32 a_s vs oracle after 100 steps: {maxabs(a[far], oa[far]):.2e} where |G| > 1e-2")
+    assert far.sum() > 1000 and maxabs(a[far], oa[far]) <= 1e-4

@@ -100,3 +100,45 @@ def test_measure_on_known_profile(orc):
     # no crossing: the whole ray solid or liquid
     o2 = O.Oracle(p).set_fields(-np.ones((n, n, n)), u)
     assert np.all(o2.measure(c, c, c)[0] == -1)
+
+
+def test_current_anisotropy_field_closed_forms(orc):
+    """a_s of the current field on planar interfaces, against the values the
+    anisotropy functions take on the crystal axes (Sec. 2 and Sec. 5.2):
+    <100> normal: cubic 1 + eps, <110> form 1 + 2eps/5 + 4gamma/7;
+    <110> normal: cubic 1 - eps, <110> form 1 - eps/10 - 13gamma/14.
+    A field that depends on x only (or on x + y only) has, by symmetry of
+    the lattice stencils, a gradient exactly along x (along (1, 1, 0))."""
+    O = orc
+    n = 24
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    eps, gam = 0.03, -0.02
+    cases = [
+        (np.tanh(2.0 * np.sin(2 * np.pi * x / n)), dict(kind=0, eps=eps), 1 + eps),
+        (np.tanh(2.0 * np.sin(2 * np.pi * (x + y) / n)), dict(kind=0, eps=eps), 1 - eps),
+        (np.tanh(2.0 * np.sin(2 * np.pi * x / n)), dict(kind=3, eps=eps, gamma=gam), 1 + 2 * eps / 5 + 4 * gam / 7),
+        (np.tanh(2.0 * np.sin(2 * np.pi * (x + y) / n)), dict(kind=3, eps=eps, gamma=gam),
+         1 - eps / 10 - 13 * gam / 14),
+    ]
+    for grad in (O.GRAD_DD, O.GRAD_FD):
+        for phi, cr, want in cases:
+            p = O.make_params(O.D3Q15_D3Q7, n, n, n, grad=grad, crystals=[O.make_crystal(**cr)])
+            o = O.Oracle(p).set_fields(phi, np.zeros_like(phi))
+            a = o.current_anisotropy()
+            G = O.gradient(p, phi)
+            moving = np.linalg.norm(G, axis=-1) > 1e-6  # away from the extrema of the sine
+            assert moving.mean() > 0.8
+            assert np.abs(a[moving] - want).max() <= 1e-13
+    # several crystals: a_s = 1 where the index is 0, the crystal's a_s elsewhere
+    p = O.make_params(O.D3Q15_D3Q7, n, n, n, crystals=[O.make_crystal(kind=0, eps=eps),
+                                                       O.make_crystal(kind=0, eps=-eps)])
+    phi = cases[0][0]
+    I = np.where(x < n / 2, 1, 2).astype(np.int32)
+    I[:, :, :3] = 0
+    o = O.Oracle(p).set_fields(phi, np.zeros_like(phi), I)
+    a = o.current_anisotropy()
+    G = O.gradient(p, phi)
+    moving = np.linalg.norm(G, axis=-1) > 1e-6
+    assert np.all(a[I == 0] == 1.0)
+    assert np.abs(a[(I == 1) & moving] - (1 + eps)).max() <= 1e-13
+    assert np.abs(a[(I == 2) & moving] - (1 - eps)).max() <= 1e-13
