@@ -55,7 +55,7 @@ WORKLOADS = {
 DTYPE = {0: "f64", 1: "f32", 2: "f32 arithmetic, f16 storage", 3: "f32 arithmetic, bf16 storage",
          4: "f32 arithmetic, f16 storage (stochastic rounding)"}
 METRIC = "fused phi+u LB step MLUPS"
-KERNEL_SOURCES = ["step_kernel.cuh", "lbpf_internal.cuh"]
+KERNEL_SOURCES = ["step_kernel.cuh", "staged_kernel.cuh", "lbpf_internal.cuh"]
 
 
 def peaks():

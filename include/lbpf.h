@@ -44,7 +44,8 @@ typedef enum {
     LBPF_EINVAL = -1,     /* invalid argument or parameter combination         */
     LBPF_ENOMEM = -2,     /* device or host allocation failed                  */
     LBPF_ECUDA = -3,      /* a CUDA runtime call failed (see lbpf_last_error)  */
-    LBPF_ETIMEOUT = -4,   /* reserved: a bounded device wait gave up           */
+    LBPF_ETIMEOUT = -4,   /* a bounded wait inside the step kernel gave up (reported by
+                             the next call that synchronises: read, measure)    */
     LBPF_ENONFINITE = -5, /* a measurement found NaN or Inf in phi or u        */
     LBPF_ERANGE = -6      /* output buffer too small                           */
 } lbpf_status;
@@ -282,7 +283,14 @@ typedef enum {
     LBPF_Q_STEP_KERNELS = 5,   /* step-kernel launches issued by lbpf_step so far     */
     LBPF_Q_TILE_ROWS = 6,      /* tile variant of the step kernel (autotuned): 8, 16 */
     LBPF_Q_SEGMENT = 7,        /* z-planes (3D) or y-rows (2D) per work item          */
-    LBPF_Q_BLOCKS = 8          /* resident blocks of the persistent step launch       */
+    LBPF_Q_BLOCKS = 8,         /* resident blocks of the persistent step launch       */
+    LBPF_Q_KERNEL = 9          /* step kernel: 0 generic (global-memory pulls, the
+                                  default), 1 staged (rows brought to shared memory by
+                                  asynchronous copies; chosen by the environment
+                                  variable LBPF_KERNEL=staged at lbpf_create for 3D
+                                  D3Q15/D3Q19 domains with 16-bit deviation storage,
+                                  nx a multiple of 8 and >= 64, one crystal; same
+                                  results bit for bit, slower on GB300)             */
 } lbpf_query_t;
 
 /* Override the work schedule of the step kernel.  Normally lbpf_create takes
@@ -294,8 +302,9 @@ typedef enum {
  * a tile along z (3D) or y (2D).  tile_rows is 8 or 16: in 3D the tile is 32
  * sites along x by tile_rows along y; in 2D it is one row of 16 * tile_rows
  * sites (128 or 256) along x.  segment (>= 1) is the number of z-planes (3D)
- * or y-rows (2D) per work item.  Results do not depend on the schedule; only
- * speed does.  A performance knob with no counterpart in the paper.
+ * or y-rows (2D) per work item (the staged kernel, LBPF_Q_KERNEL = 1, takes
+ * only tile_rows = 8).  Results do not depend on the schedule; only speed
+ * does.  A performance knob with no counterpart in the paper.
  * Errors: LBPF_EINVAL. */
 int lbpf_set_schedule(lbpf_ctx* ctx, int tile_rows, int segment);
 

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build", platform.machine())  # objects of this host
 LIB = os.path.join(HERE, "liblbpf.so")
 SOURCES = ["lbpf_api.cu", "lbpf_fields.cu", "lbpf_d2q9.cu", "lbpf_d3q15.cu", "lbpf_d3q19.cu", "lbpf_d3q27.cu",
            "lbpf_static.cu", "lbpf_nn.cu", "lbpf_unet.cu"]
-HEADERS = ["lbpf_internal.cuh", "step_kernel.cuh", "aux_kernels.cuh", "lbpf_nn.cuh"]
+HEADERS = ["lbpf_internal.cuh", "step_kernel.cuh", "staged_kernel.cuh", "aux_kernels.cuh", "lbpf_nn.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 

@@ -4,7 +4,7 @@
 // them is on the per-step path.
 #pragma once
 
-#include "step_kernel.cuh"
+#include "staged_kernel.cuh"
 
 namespace lbpf {
 
@@ -273,8 +273,40 @@ struct LauncherImpl {
     static size_t smem(int v) { return v == 0 ? smem_v<0>() : smem_v<1>(); }
     static cudaError_t prepare(int v)
     {
+        if constexpr (kStaged) {
+            if (v == 0) {
+                cudaError_t e = cudaFuncSetAttribute(step_kernel_staged<PL, UL, S>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)staged_smem_bytes<PL, UL, S>());
+                if (e != cudaSuccess) return e;
+            }
+        }
         return v == 0 ? cudaFuncSetAttribute(kernel<0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<0>())
                       : cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
+    }
+    // the staged kernel: 3D, 16-bit deviation storage, lattices whose staging
+    // fits two blocks per SM (D3Q15, D3Q19)
+    static constexpr bool kStaged = PL::D == 3 && S::dev && (PL::Q == 15 || PL::Q == 19);
+    static cudaError_t step_staged(const StepArgs& a, int n_blocks, cudaStream_t s)
+    {
+        if constexpr (kStaged) {
+            step_kernel_staged<PL, UL, S><<<n_blocks, 256, staged_smem_bytes<PL, UL, S>(), s>>>(a);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+    static int staged_blocks_per_sm()
+    {
+        int nb = 0;
+        if constexpr (kStaged) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel_staged<PL, UL, S>, 256,
+                                                              staged_smem_bytes<PL, UL, S>()) != cudaSuccess) {
+                cudaGetLastError();
+                return 1;
+            }
+        }
+        return nb > 0 ? nb : 1;
     }
     static int blocks_per_sm(int v)
     {
@@ -317,7 +349,10 @@ struct LauncherImpl {
     }
     static const Launchers* get()
     {
-        static const Launchers L = {&step, &smem, &prepare, &blocks_per_sm, &heat_sync, &equilibrate, &read_u, &read_pop, &read_as, PL::Q, UL::Q, PL::D};
+        static const Launchers L = {&step,     &smem,           &prepare,  &blocks_per_sm,
+                                    kStaged ? &step_staged : nullptr,      &staged_blocks_per_sm,
+                                    &heat_sync, &equilibrate,   &read_u,   &read_pop,
+                                    &read_as,  PL::Q,          UL::Q,     PL::D};
         return &L;
     }
 };

@@ -43,6 +43,7 @@ struct lbpf_ctx {
     int* d_counters = nullptr;
     int n_items = 0, n_blocks = 0, items_cap = 0;
     int tile_v = 0, seg_len = 0, sms = 1;
+    bool staged = false;  // step kernel with bulk-copy staging (staged_kernel.cuh)
     // graphs of kGraphSteps steady-state launches, keyed by (cur, fcur, acur)
     cudaGraphExec_t graphs[8] = {};
     bool graphs_off = false;
@@ -138,12 +139,17 @@ static long long column_units(const lbpf_ctx* c, int v)
     return units;
 }
 
+static int blocks_per_sm(const lbpf_ctx* c, int v)
+{
+    return c->staged ? c->L->staged_blocks_per_sm() : c->L->blocks_per_sm(v);
+}
+
 // Segment length balancing the per-item prologue (two extra planes) against
 // the tail of the dynamic schedule: L ~ sqrt(5 units / resident blocks).
 static int default_segment(const lbpf_ctx* c, int v)
 {
     if (LBPF_SEGMENT > 0) return LBPF_SEGMENT;
-    const double G = (double)c->L->blocks_per_sm(v) * c->sms;
+    const double G = (double)blocks_per_sm(c, v) * c->sms;
     int L = (int)std::lround(std::sqrt(5.0 * (double)column_units(c, v) / G));
     return L < 8 ? 8 : (L > 256 ? 256 : L);
 }
@@ -183,7 +189,7 @@ static int set_schedule(lbpf_ctx* c, int v, int seg)
     CK(cudaMemcpyAsync(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->n_items = (int)items.size();
-    long long G = (long long)c->L->blocks_per_sm(v) * c->sms;
+    long long G = (long long)blocks_per_sm(c, v) * c->sms;
     c->n_blocks = (int)(G < c->n_items ? G : c->n_items);
     c->tile_v = v;
     c->seg_len = seg;
@@ -210,8 +216,8 @@ static std::string tune_key(const lbpf_ctx* c)
         h ^= (unsigned char)*p;
         h *= 1099511628211ULL;
     }
-    snprintf(buf, sizeof(buf), "s2-lat%d-prec%d-grad%d-dom%d-%016llx-sm%d", c->lattice, c->precision, c->grad,
-             c->n_domains, h, c->sms);
+    snprintf(buf, sizeof(buf), "s2-lat%d-prec%d-grad%d-dom%d-%016llx-sm%d-k%d", c->lattice, c->precision, c->grad,
+             c->n_domains, h, c->sms, c->staged ? 1 : 0);
     return buf;
 }
 
@@ -247,7 +253,9 @@ static double time_schedule(lbpf_ctx* c, int launches)
     for (int k = 0; k < launches + 2; ++k) {
         if (cudaMemsetAsync(c->d_counters + c->cur, 0, sizeof(int), c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
-        if (c->L->step(c->tile_v, a, c->n_blocks, c->stream) != cudaSuccess) break;
+        if ((c->staged ? c->L->step_staged(a, c->n_blocks, c->stream)
+                       : c->L->step(c->tile_v, a, c->n_blocks, c->stream)) != cudaSuccess)
+            break;
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -294,7 +302,7 @@ static int autotune(lbpf_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     double best_t = 1e30, rule_t = 1e30;
     int best_v = 0, best_seg = default_segment(c, 0);
-    for (int v = 0; v < kNumTileVariants; ++v) {
+    for (int v = 0; v < (c->staged ? 1 : kNumTileVariants); ++v) {
         const int L0 = default_segment(c, v);
         const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
         for (int j = 0; j < 3; ++j) {
@@ -430,6 +438,13 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         }
     }
     if (rc == LBPF_OK) {
+        // the staged kernel (opt-in: it measured slower than the generic one,
+        // see staged_kernel.cuh) needs 16-byte aligned row copies (nx a
+        // multiple of 8), rows wider than the staged 48-site window, one crystal
+        const char* kenv = getenv("LBPF_KERNEL");
+        c->staged = L->step_staged != nullptr && kenv && strcmp(kenv, "staged") == 0;
+        for (const DomainDev& h : c->dd)
+            if (h.nx % 8 != 0 || h.nx < 64 || h.use_index) c->staged = false;
         if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
             c->sms = 1;
         for (int v = 0; v < kNumTileVariants && rc == LBPF_OK; ++v) {
@@ -437,8 +452,8 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
             if (e != cudaSuccess) rc = fail(c, LBPF_ECUDA, "lbpf_create: kernel attribute: %s", cudaGetErrorString(e));
         }
     }
-    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 4);
-    if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 4, c->stream) != cudaSuccess)
+    if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_counters), sizeof(int) * 8);
+    if (rc == LBPF_OK && cudaMemsetAsync(c->d_counters, 0, sizeof(int) * 8, c->stream) != cudaSuccess)
         rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
     if (rc == LBPF_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->d_dd), sizeof(DomainDev) * n_domains);
     if (rc == LBPF_OK) {
@@ -474,6 +489,16 @@ static int check_ctx(lbpf_ctx* c, int domain)
     if (!c) return fail(nullptr, LBPF_EINVAL, "context is NULL");
     if (domain < 0 || domain >= c->n_domains) return fail(c, LBPF_EINVAL, "domain %d out of range", domain);
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LBPF_ECUDA, "cudaSetDevice(%d) failed", c->device);
+    return LBPF_OK;
+}
+
+// The device error word (set by a bounded wait of the staged kernel that
+// gave up); read after the stream has been synchronised.
+static int device_error(lbpf_ctx* c)
+{
+    int w = 0;
+    CK(cudaMemcpy(&w, c->d_counters + 4, sizeof(int), cudaMemcpyDeviceToHost));
+    if (w) return fail(c, LBPF_ETIMEOUT, "a bounded wait in the step kernel gave up (device error word %d)", w);
     return LBPF_OK;
 }
 
@@ -564,7 +589,10 @@ static int launch_step(lbpf_ctx* c)
     a.acur = c->acur;
     a.collide = c->lagged;
     a.grad = c->grad;
-    CK(c->L->step(c->tile_v, a, c->n_blocks, c->stream));
+    if (c->staged)
+        CK(c->L->step_staged(a, c->n_blocks, c->stream));
+    else
+        CK(c->L->step(c->tile_v, a, c->n_blocks, c->stream));
     c->cur ^= 1;
     c->acur ^= 1;
     if (c->lagged) c->fcur ^= 1;
@@ -685,7 +713,7 @@ extern "C" int lbpf_read_fields(lbpf_ctx* c, int domain, unsigned mask, void* ou
         o += bytes;
     }
     CK(cudaStreamSynchronize(c->stream));
-    return LBPF_OK;
+    return device_error(c);
 }
 
 extern "C" int lbpf_read_field(lbpf_ctx* c, int domain, int field, void* out, int out_on_device, size_t out_bytes)
@@ -744,6 +772,7 @@ extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, dou
     CK(cudaStreamSynchronize(c->stream));
     if (tip6)
         for (int k = 0; k < 6; ++k) tip6[k] = hv[3 + k];
+    if ((rc = device_error(c))) return rc;
     if (solid_fraction) *solid_fraction = hv[0] / (double)h.n;
     if (conserved) *conserved = hv[1];
     if (hv[2] > 0) return fail(c, LBPF_ENONFINITE, "lbpf_measure: %.0f non-finite values in phi or u", hv[2]);
@@ -789,6 +818,7 @@ extern "C" int lbpf_set_schedule(lbpf_ctx* c, int tile_rows, int segment)
     for (int k = 0; k < kNumTileVariants; ++k)
         if (kTileRows[k] == tile_rows) v = k;
     if (v < 0 || segment < 1) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: tile_rows must be 8 or 16, segment >= 1");
+    if (c->staged && v != 0) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: the staged kernel uses 8-row tiles");
     CK(cudaStreamSynchronize(c->stream));
     c->tune_pending = false;
     c->tuned = "set";
@@ -821,6 +851,7 @@ extern "C" int lbpf_query(const lbpf_ctx* c, int what, double* value)
     case LBPF_Q_TILE_ROWS: v = kTileRows[c->tile_v]; break;
     case LBPF_Q_SEGMENT: v = c->seg_len; break;
     case LBPF_Q_BLOCKS: v = c->n_blocks; break;
+    case LBPF_Q_KERNEL: v = c->staged ? 1 : 0; break;
     default: return fail(const_cast<lbpf_ctx*>(c), LBPF_EINVAL, "lbpf_query: unknown property %d", what);
     }
     *value = v;

@@ -224,7 +224,8 @@ struct StepArgs {
     const DomainDev* doms;
     const WorkItem* items;
     int n_items;
-    int* counters;         // [0..1] work counters, [2..3] rounding seeds, used alternately
+    int* counters;         // [0..1] work counters, [2..3] rounding seeds, used alternately;
+                           // [4] device error word (1: a bounded wait of the staged kernel gave up)
     int cur;    // g / phi / I buffer holding time n (new = cur ^ 1)
     int fcur;   // f buffer read (f^{n-1} when collide, f^n when load)
     int acur;   // aux buffer read (new = acur ^ 1)
@@ -372,6 +373,10 @@ struct Launchers {
     cudaError_t (*prepare)(int v);
     // Resident blocks per SM of variant v.
     int (*blocks_per_sm)(int v);
+    // Staged step kernel (staged_kernel.cuh; tile 32 x 8 of variant 0), or
+    // nullptr where it is not built (2D, full storage, D3Q27).
+    cudaError_t (*step_staged)(const StepArgs& a, int n_blocks, cudaStream_t s);
+    int (*staged_blocks_per_sm)();
     // Heat step alone, lagged -> synced state of one domain (f^{n-1}, aux^{n-1},
     // phi^n -> f^n [+ aux^n]).
     cudaError_t (*heat_sync)(const DomainDev* d, int cur, int fcur, int acur, cudaStream_t s);

@@ -24,7 +24,7 @@ LBPF_AS_CUBIC100, LBPF_AS_ANGLE, LBPF_AS_Y66, LBPF_AS_HOYT110, LBPF_AS_S111 = 0,
 LBPF_FIELD_PHI, LBPF_FIELD_U, LBPF_FIELD_INDEX, LBPF_FIELD_AS = 0, 1, 2, 3
 LBPF_READ_PHI, LBPF_READ_U, LBPF_READ_AS, LBPF_READ_INDEX = 1, 2, 4, 8
 (LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS,
- LBPF_Q_TILE_ROWS, LBPF_Q_SEGMENT, LBPF_Q_BLOCKS) = range(9)
+ LBPF_Q_TILE_ROWS, LBPF_Q_SEGMENT, LBPF_Q_BLOCKS, LBPF_Q_KERNEL) = range(10)
 LBPF_MAX_CRYSTALS = 16
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_fields", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
