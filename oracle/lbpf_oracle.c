@@ -59,10 +59,15 @@ typedef struct {
     double phi0;
 } orc_crystal;
 
+/* Boundary bits (orc_params.bc): a set bit makes both ends of that axis
+ * zero-flux walls; a clear bit leaves the axis periodic. */
+enum { ORC_WALL_X = 1, ORC_WALL_Y = 2, ORC_WALL_Z = 4 };
+
 typedef struct {
     int lattice;
     int grad; /* 0: directional derivatives (Sec. 4.2), 1: central finite differences */
     int nx, ny, nz;
+    int bc;   /* ORC_WALL_* bits; 0 = periodic box */
     double dx, dt, W0, tau0, kappa, lambda, delta, xi;
     int n_crystals;
     orc_crystal crystals[ORC_MAXC];
@@ -236,7 +241,7 @@ int orc_lattice(int lattice, int which, int* D, int* Q, int* e, double* w, doubl
 }
 
 /* ------------------------------------------------------------------------- */
-/* Grid helpers (periodic wrap).                                              */
+/* Grid helpers: periodic wrap, or reflection at zero-flux walls.             */
 /* ------------------------------------------------------------------------- */
 
 static int wrap(int i, int n)
@@ -245,9 +250,58 @@ static int wrap(int i, int n)
     return r < 0 ? r + n : r;
 }
 
+/* Reading (boundary conditions, Sec. 3.3): the paper imposes zero fluxes on
+ * all walls for both equations by bounce-back.  A wall is taken as a mirror
+ * plane through the boundary nodes: a node at distance k outside the wall is
+ * the image of the node at distance k inside it (index -k -> k, and
+ * n - 1 + k -> n - 1 - k), so the gradient stencil reads phi of the image
+ * there (zero normal derivative), and a population arriving from beyond a
+ * wall is the one streamed to the same node in the mirrored direction
+ * (fill_walls).  A population streamed out through a wall is discarded, so
+ * the non-local term of Eq. (LBE_Eq_Phase) never needs a value beyond the
+ * wall.  With these rules an octant run with walls on the symmetry planes is
+ * exactly a part of the mirror-symmetric run (Sec. 5.3).  The paper prints
+ * the bounce-back with the opposite direction i' (f_i = f_i'); for the axis
+ * populations (all of D2Q5 and D3Q7) the mirror and the opposite direction
+ * coincide, for diagonal ones only the mirror keeps the wall a symmetry
+ * plane. */
+static int reflect(int i, int n)
+{
+    while (i < 0 || i > n - 1) i = (i < 0) ? -i : 2 * (n - 1) - i;
+    return i;
+}
+
+static int map_axis(const orc_params* p, int axis, int i)
+{
+    const int n = axis == 0 ? p->nx : (axis == 1 ? p->ny : p->nz);
+    return (p->bc & (1 << axis)) ? reflect(i, n) : wrap(i, n);
+}
+
 static long site(const orc_params* p, int x, int y, int z)
 {
-    return ((long)wrap(z, p->nz) * p->ny + wrap(y, p->ny)) * p->nx + wrap(x, p->nx);
+    return ((long)map_axis(p, 2, z) * p->ny + map_axis(p, 1, y)) * p->nx + map_axis(p, 0, x);
+}
+
+/* Bit a of the result is set when coordinate a of (x, y, z) lies outside a
+ * wall of axis a. */
+static int outside_walls(const orc_params* p, int x, int y, int z)
+{
+    const int c[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
+    int m = 0;
+    for (int a = 0; a < 3; ++a)
+        if ((p->bc & (1 << a)) && (c[a] < 0 || c[a] > n[a] - 1)) m |= 1 << a;
+    return m;
+}
+
+/* The direction of lattice L whose velocity is e_i with the components of
+ * the axes in `mask` reversed (the mirror image of e_i in those walls). */
+static int reflect_dir(const orc_lattice_t* L, int i, int mask)
+{
+    int t[3];
+    for (int a = 0; a < 3; ++a) t[a] = (mask & (1 << a)) ? -L->e[i][a] : L->e[i][a];
+    for (int j = 0; j < L->Q; ++j)
+        if (L->e[j][0] == t[0] && L->e[j][1] == t[1] && L->e[j][2] == t[2]) return j;
+    return -1;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -512,7 +566,8 @@ static double periodic_delta(double d, int n)
  * (R_s - d_s)/(sqrt(2) W0), the equilibrium width of the model; with R, d in
  * lattice units this is (R - d) dx / (sqrt(2) W0).  Several seeds combine by
  * the maximum of their profiles; distances are minimum-image distances on the
- * periodic box.  The index field starts at I = 1 + crystal of the seed with
+ * periodic box (plain distances along walled axes).  The index field starts
+ * at I = 1 + crystal of the seed with
  * the largest profile wherever phi > 0 or |grad phi| > xi, and 0 elsewhere. */
 int orc_seed(orc_state* s, const double* seeds, int n_seeds)
 {
@@ -526,9 +581,11 @@ int orc_seed(orc_state* s, const double* seeds, int n_seeds)
                 int bestc = 0;
                 for (int j = 0; j < n_seeds; ++j) {
                     const double* sd = &seeds[5 * j];
-                    double ddx = periodic_delta(x - sd[0], p->nx);
-                    double ddy = periodic_delta(y - sd[1], p->ny);
-                    double ddz = (s->Lg.D == 3) ? periodic_delta(z - sd[2], p->nz) : 0.0;
+                    /* minimum image along periodic axes, plain distance along walled ones */
+                    double ddx = (p->bc & ORC_WALL_X) ? x - sd[0] : periodic_delta(x - sd[0], p->nx);
+                    double ddy = (p->bc & ORC_WALL_Y) ? y - sd[1] : periodic_delta(y - sd[1], p->ny);
+                    double ddz = (s->Lg.D == 3) ? ((p->bc & ORC_WALL_Z) ? z - sd[2] : periodic_delta(z - sd[2], p->nz))
+                                                : 0.0;
                     double d = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
                     double v = tanh((sd[3] - d) * p->dx / (sqrt(2.0) * p->W0));
                     if (v > best) {
@@ -601,6 +658,25 @@ static int index_update(const orc_state* s, int x, int y, int z, const double G[
     return 0;
 }
 
+/* After streaming: at every node, each population whose source node lies
+ * beyond a wall takes the value of the population streamed to the same node
+ * in the direction reflected in that wall (or walls, at edges and corners). */
+static void fill_walls(const orc_state* s, const orc_lattice_t* L, double* pop)
+{
+    const orc_params* p = &s->p;
+    const long n = s->n;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = site(p, x, y, z);
+                for (int i = 0; i < L->Q; ++i) {
+                    const int* e = L->e[i];
+                    int out = outside_walls(p, x - e[0], y - e[1], z - e[2]);
+                    if (out) pop[(long)i * n + k] = pop[(long)reflect_dir(L, i, out) * n + k];
+                }
+            }
+}
+
 /* One time step: the phase-field scheme (Sec. 3.2) then the heat scheme
  * (Sec. 3.1), in the order the paper prescribes (heat after phase field). */
 static void step_once(orc_state* s)
@@ -645,6 +721,9 @@ static void step_once(orc_state* s)
                 double Qphi = (phi - p->lambda * u * (1.0 - phi * phi)) * (1.0 - phi * phi);
                 for (int i = 0; i < Lg->Q; ++i) {
                     const int* e = Lg->e[i];
+                    /* a population streamed beyond a wall leaves the box; the
+                     * walls send back its mirror image (fill_walls) */
+                    if (outside_walls(p, x + e[0], y + e[1], z + e[2])) continue;
                     long kn = site(p, x + e[0], y + e[1], z + e[2]);
                     double gi = s->g[(long)i * n + k];
                     double gi_next = s->g[(long)i * n + kn];
@@ -654,6 +733,10 @@ static void step_once(orc_state* s)
                     s->gnew[(long)i * n + kn] = rhs / a2;
                 }
             }
+    /* Bounce-back at the walls (Sec. 3.3), read as specular reflection: a
+     * population whose source node lies beyond a wall is the one streamed to
+     * the same node in the reflected direction. */
+    if (p->bc) fill_walls(s, Lg, s->gnew);
     /* phi(t + dt), Eq. (Def_M0_Phi) */
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) {
@@ -680,9 +763,11 @@ static void step_once(orc_state* s)
                     long kn = site(p, x + e[0], y + e[1], z + e[2]);
                     double fi = s->f[(long)i * n + k];
                     double feq = Lu->w[i] * u;
-                    s->fnew[(long)i * n + kn] = fi - (fi - feq) / eta_u + Lu->w[i] * Qu * p->dt;
+                    if (!outside_walls(p, x + e[0], y + e[1], z + e[2])) /* else it leaves the box */
+                        s->fnew[(long)i * n + kn] = fi - (fi - feq) / eta_u + Lu->w[i] * Qu * p->dt;
                 }
             }
+    if (p->bc) fill_walls(s, Lu, s->fnew);
     /* u(t + dt), Eq. (Temperature_LB) */
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) {
@@ -753,13 +838,16 @@ int orc_anisotropy_field(const orc_state* s, double* a)
 
 /* Tip position along one axis direction from the integer site c.
  * The paper defines only the tip velocity V_p (Sec. 3.4).  Reading: the tip
- * is the outermost crossing phi = 0 on the ray c + k d, k = 0 .. n/2 - 1,
+ * is the outermost crossing phi = 0 on the ray c + k d, k = 0 .. n/2 - 1
+ * (up to the wall on a walled axis),
  * located by linear interpolation, x_tip = k + phi_k / (phi_k - phi_{k+1});
  * -1 when the ray has no crossing. */
 static double tip_along(const orc_state* s, const int c[3], int axis, int sign)
 {
     const orc_params* p = &s->p;
-    int len = (axis == 0 ? p->nx : axis == 1 ? p->ny : p->nz) / 2;
+    const int na = axis == 0 ? p->nx : axis == 1 ? p->ny : p->nz;
+    /* half the box on a periodic axis; up to the wall on a walled one */
+    int len = (p->bc & (1 << axis)) ? (sign > 0 ? na - 1 - c[axis] : c[axis]) : na / 2;
     double tip = -1.0;
     for (int k = 0; k + 1 <= len; ++k) {
         int a0[3] = {c[0], c[1], c[2]}, a1[3] = {c[0], c[1], c[2]};
@@ -775,7 +863,9 @@ static double tip_along(const orc_state* s, const int c[3], int axis, int sign)
 /* tip6: +x, -x, +y, -y, +z, -z tip distances from the centre site (the z
  * entries are -1 in 2D); solid_fraction = mean of (1 + phi)/2;
  * conserved = sum over sites of (u - phi/2), which the scheme keeps constant
- * on a periodic box (integral of Eq. (Temp_Ramirez)). */
+ * in a periodic or closed box (integral of Eq. (Temp_Ramirez) with zero
+ * flux); nodes on walls count 1/2 per walled coordinate (they lie on the
+ * mirror planes). */
 int orc_measure(const orc_state* s, int cx, int cy, int cz, double* tip6, double* solid_fraction,
                 double* conserved)
 {
@@ -789,10 +879,20 @@ int orc_measure(const orc_state* s, int cx, int cy, int cz, double* tip6, double
         tip6[2 * a + 1] = tip_along(s, c, a, -1);
     }
     double sf = 0.0, cs = 0.0;
-    for (long k = 0; k < s->n; ++k) {
-        sf += 0.5 * (1.0 + s->phi[k]);
-        cs += s->u[k] - 0.5 * s->phi[k];
-    }
+    const orc_params* p = &s->p;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = site(p, x, y, z);
+                /* a node on a wall is shared with its mirror image: weight
+                 * 1/2 per walled coordinate at a wall (the trapezoid rule) */
+                double wgt = 1.0;
+                if ((p->bc & ORC_WALL_X) && (x == 0 || x == p->nx - 1)) wgt *= 0.5;
+                if ((p->bc & ORC_WALL_Y) && (y == 0 || y == p->ny - 1)) wgt *= 0.5;
+                if ((p->bc & ORC_WALL_Z) && s->Lg.D == 3 && (z == 0 || z == p->nz - 1)) wgt *= 0.5;
+                sf += 0.5 * (1.0 + s->phi[k]);
+                cs += wgt * (s->u[k] - 0.5 * s->phi[k]);
+            }
     *solid_fraction = sf / (double)s->n;
     *conserved = cs;
     return 0;

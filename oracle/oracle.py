@@ -31,6 +31,8 @@ D2Q9_D2Q5, D3Q15_D3Q7, D3Q19_D3Q7, D3Q27_D3Q7, D2Q9_D2Q5P = range(5)
 AS_CUBIC100, AS_ANGLE, AS_Y66, AS_HOYT110, AS_S111 = range(5)
 # Gradient operators.
 GRAD_DD, GRAD_FD = 0, 1
+# Boundary bits: zero-flux walls at both ends of an axis (0: periodic box).
+WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 
 # Thin-interface coefficients, Eqs. (Capillary-Length) and (Kinetic-Coeff):
 # a1 = 5 sqrt(2) / 8 and a2 ~ 0.6267 (the paper's lambda* = 1.59566 kappa
@@ -68,7 +70,7 @@ class Crystal(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("grad", C.c_int),
-                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("W0", C.c_double),
                 ("tau0", C.c_double), ("kappa", C.c_double), ("lam", C.c_double),
                 ("delta", C.c_double), ("xi", C.c_double),
@@ -130,11 +132,12 @@ def make_crystal(kind=AS_CUBIC100, eps=0.0, gamma=0.0, q=4, phi0=0.0) -> Crystal
 
 
 def make_params(lattice_pair, nx, ny, nz=1, *, grad=GRAD_DD, dx=1.0, dt=1.0, W0=1.0, tau0=1.0,
-                kappa=1.0, lam=None, delta=0.0, xi=1e-7, crystals=(None,)) -> Params:
+                kappa=1.0, lam=None, delta=0.0, xi=1e-7, crystals=(None,), bc=0) -> Params:
     p = Params()
     p.lattice = lattice_pair
     p.grad = grad
     p.nx, p.ny, p.nz = nx, ny, nz
+    p.bc = bc
     p.dx, p.dt, p.W0, p.tau0, p.kappa = dx, dt, W0, tau0, kappa
     p.lam = lambda_star(kappa, tau0, W0) if lam is None else lam
     p.delta = delta
