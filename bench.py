@@ -48,6 +48,11 @@ WORKLOADS = {
     "c3-512-fp16dev-sr": ("3D 512^3 periodic, D3Q15/D3Q7, FP32 arithmetic with FP16 deviation storage rounded "
                           "stochastically, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 4, 512),
     "c3-512-fp32": ("3D 512^3 periodic, D3Q15/D3Q7, FP32, <110> form eps=0, gamma=-0.02, Delta=0.4, seed R=8", 1, 1, 512),
+    "octant-351-fp32": ("3D octant of dendrite B (Sec. 5.3): 351^3, zero-flux walls on all faces, seed R=8 at the "
+                        "origin, D3Q15/D3Q7, FP32, <110> form eps=0, gamma=-0.02, Delta=0.25", 1, 1, 351),
+    "octant-351-fp16dev": ("3D octant of dendrite B (Sec. 5.3): 351^3, zero-flux walls on all faces, seed R=8 at the "
+                           "origin, D3Q15/D3Q7, FP32 arithmetic with FP16 deviation storage, <110> form eps=0, "
+                           "gamma=-0.02, Delta=0.25", 1, 2, 351),
     "c4-batch64-fp32": ("batched 2D multi-crystal: 64 periodic domains, sides U{128..1024} (24.4 M sites), D2Q9/D2Q5, "
                         "FP32, 1-12 seeds each with its own angle-form crystal (q=4, theta, eps), Delta per domain, "
                         "one launch per step, CUDA graphs", 0, 1, 0),
@@ -180,15 +185,23 @@ def make_batch(L, W, stream, precision=1):
     return s, {"centre": (int(c[0]), int(c[1]), 0)}
 
 
+def workload_recipe(W, workload, n):
+    if workload.startswith("c2"):
+        return W.c2(n)
+    if workload.startswith("octant"):
+        return W.octant(n)
+    return W.c3(n, eps=0.0, gamma=-0.02)
+
+
 def make_solver(L, W, workload, stream, size=0):
     if workload.startswith("c4"):
         return make_batch(L, W, stream)
     desc, lattice, precision, n = WORKLOADS[workload]
     n = size or n
-    w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
+    w = workload_recipe(W, workload, n)
     prm = dict(w["params"])
     lam = prm.pop("lam")
-    dom = L.make_domain(n, n, n, lam=lam, crystals=[L.make_crystal(**w["aniso"])], **prm)
+    dom = L.make_domain(n, n, n, lam=lam, crystals=[L.make_crystal(**w["aniso"])], bc=w.get("bc", 0), **prm)
     s = L.Solver(dom, lattice, L.LBPF_GRAD_DD, precision, stream=stream)
     s.seed(w["seeds"])
     return s, w
@@ -220,12 +233,13 @@ def oracle_sample(workload: str, n: int):
                           **prm)
         o = O.Oracle(p).seed([list(s) for s in w["seeds"]])
         return o, side * side, f"first domain of the batch ({side}^2, {len(w['seeds'])} crystals)"
-    w = W.c2(n) if workload.startswith("c2") else W.c3(n, eps=0.0, gamma=-0.02)
+    w = workload_recipe(W, workload, n)
     prm = dict(w["params"])
     lam = prm.pop("lam")
-    p = O.make_params(lattice, n, n, n, lam=lam, crystals=[O.make_crystal(**w["aniso"])], **prm)
+    p = O.make_params(lattice, n, n, n, lam=lam, crystals=[O.make_crystal(**w["aniso"])], bc=w.get("bc", 0), **prm)
     o = O.Oracle(p).seed([list(s) for s in w["seeds"]])
-    return o, n ** 3, f"{n}^3 periodic crop of the workload"
+    kind = "walled octant" if w.get("bc") else "periodic crop"
+    return o, n ** 3, f"{n}^3 {kind} of the workload"
 
 
 def cpu_oracle_rate(workload: str, budget_s: float, n: int = 64, max_steps: int | None = None):

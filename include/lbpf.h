@@ -25,8 +25,9 @@
  *     call.  The context owns all device memory it allocates and borrows the
  *     CUDA stream given to lbpf_create (NULL = the legacy default stream).
  *   - Calls on one context must not overlap (one host thread at a time).
- *   - Boundaries are periodic in every direction (the paper's own runs use
- *     zero-flux bounce-back walls, Sec. 3.3; not provided by this library).
+ *   - Boundaries are periodic, or zero-flux walls per axis (lbpf_domain.bc):
+ *     the bounce-back walls of Sec. 3.3, taken as mirror planes through the
+ *     boundary nodes (see LBPF_BC_WALL_X).
  */
 #ifndef LBPF_H
 #define LBPF_H
@@ -119,9 +120,28 @@ typedef struct {
 
 #define LBPF_MAX_CRYSTALS 16
 
-/* One periodic domain and its model parameters (Sec. 2, Sec. 3). */
+/* Boundary bits of lbpf_domain.bc.  A set bit makes both ends of that axis
+ * zero-flux walls (Sec. 3.3: zero fluxes on all boundaries, imposed by
+ * bounce-back, for both equations); a clear bit leaves the axis periodic.
+ * A wall is a mirror plane through the boundary nodes: the gradient stencil
+ * reads phi of the mirror image beyond it (zero normal derivative), and a
+ * population arriving from beyond it is the one streamed to the same node in
+ * the mirrored direction.  For the axis populations (all of D2Q5 and D3Q7)
+ * this is the printed rule f_i = f_i', i' the opposite direction; for the
+ * diagonal populations the mirror keeps the wall a symmetry plane, so that a
+ * box with walls on the symmetry planes is exactly one octant (quadrant) of
+ * the symmetric crystal, as in the octant runs of Sec. 5.3.  Seeds use plain
+ * (not periodic) distances along walled axes; the conserved sum of
+ * lbpf_measure then weights nodes on a wall by 1/2 per walled coordinate.  A
+ * walled axis needs at least 3 sites. */
+#define LBPF_BC_WALL_X 1
+#define LBPF_BC_WALL_Y 2
+#define LBPF_BC_WALL_Z 4
+
+/* One domain and its model parameters (Sec. 2, Sec. 3). */
 typedef struct {
     int nx, ny, nz;  /* sites; nz = 1 for 2D lattices; each >= 2 in 3D, nx, ny >= 2 */
+    int bc;          /* LBPF_BC_WALL_* bits; 0 = periodic in every direction   */
     double dx, dt;   /* space and time steps                                       */
     double W0, tau0; /* interface thickness and kinetic time, Eq. (PhaseField_KarmaRappel) */
     double kappa;    /* thermal diffusivity, Eq. (Temp_Ramirez)                    */
@@ -243,12 +263,14 @@ int lbpf_read_populations(lbpf_ctx* ctx, int domain, int which, void* out, int o
 /* Measurements of one domain (synchronises the stream):
  *   tip6[6]:  distance from the site (cx, cy, cz) to the outermost phi = 0
  *             crossing along +x, -x, +y, -y, +z, -z (linear interpolation,
- *             rays of half the domain length; -1 when a ray has no crossing;
- *             the z entries are -1 in 2D).  The paper defines the tip velocity
+ *             rays of half the domain length on periodic axes, up to the
+ *             wall on walled ones; -1 when a ray has no crossing; the z
+ *             entries are -1 in 2D).  The paper defines the tip velocity
  *             V_p from the tip position (Sec. 3.4) but not the position itself.
  *   solid_fraction: mean of (1 + phi)/2.
  *   conserved: sum over sites of (u - phi/2), accumulated in FP64; constant
- *             on a periodic box (integral of Eq. (Temp_Ramirez)).
+ *             in a periodic or walled box (integral of Eq. (Temp_Ramirez)
+ *             with zero flux); sites on walls count 1/2 per walled coordinate.
  * Any output pointer may be NULL.  Returns LBPF_ENONFINITE if phi or u holds
  * a NaN or Inf. */
 int lbpf_measure(lbpf_ctx* ctx, int domain, int cx, int cy, int cz, double* tip6,

@@ -665,6 +665,8 @@ static void fill_walls(const orc_state* s, const orc_lattice_t* L, double* pop)
 {
     const orc_params* p = &s->p;
     const long n = s->n;
+    /* each fill reads a population of the same node that is not filled */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {

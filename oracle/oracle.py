@@ -270,15 +270,23 @@ def tip_velocity(times, positions):
     return float(np.polyfit(t, x, 1)[0])
 
 
-def ray_crossing(phi, centre, axis, sign, offsets):
+def _reflect(v, n):
+    while v < 0 or v > n - 1:
+        v = -v if v < 0 else 2 * (n - 1) - v
+    return v
+
+
+def ray_crossing(phi, centre, axis, sign, offsets, bc=0):
     """Outermost phi = 0 crossing (linear interpolation) along the ray from
     `centre` shifted by `offsets` (dict axis -> shift), in direction sign along
-    `axis`, over half the box; -1 when there is none.  phi is (nz, ny, nx)."""
+    `axis`, over half the box (up to the wall along a walled axis, bc bit
+    1 << axis; offsets beyond a wall are reflected); -1 when there is none.
+    phi is (nz, ny, nx)."""
     shape = phi.shape[::-1]  # (nx, ny, nz)
     c = list(centre)
     for ax, sh in offsets.items():
-        c[ax] = (c[ax] + sh) % shape[ax]
-    length = shape[axis] // 2
+        c[ax] = _reflect(c[ax] + sh, shape[ax]) if bc >> ax & 1 else (c[ax] + sh) % shape[ax]
+    length = (shape[axis] - 1 - c[axis] if sign > 0 else c[axis]) if bc >> axis & 1 else shape[axis] // 2
     best = -1.0
     for k in range(length):
         p0i, p1i = list(c), list(c)
@@ -291,9 +299,10 @@ def ray_crossing(phi, centre, axis, sign, offsets):
     return best
 
 
-def tip_radius(phi, centre, direction, J=3):
+def tip_radius(phi, centre, direction, J=3, bc=0):
     """Tip radius (lattice units) of the tip along direction 0..5
-    (+x, -x, +y, -y, +z, -z) from the crossings at transverse offsets |j| <= J."""
+    (+x, -x, +y, -y, +z, -z) from the crossings at transverse offsets |j| <= J
+    (bc: wall bits, see ray_crossing)."""
     axis, sign = direction // 2, (1 if direction % 2 == 0 else -1)
     dim = 3 if phi.shape[0] > 1 else 2
     planes = [a for a in range(dim) if a != axis]
@@ -301,7 +310,7 @@ def tip_radius(phi, centre, direction, J=3):
     for tr in planes:
         js, xs = [], []
         for j in range(-J, J + 1):
-            x = ray_crossing(phi, centre, axis, sign, {tr: j})
+            x = ray_crossing(phi, centre, axis, sign, {tr: j}, bc)
             if x >= 0:
                 js.append(j * j)
                 xs.append(x)

@@ -24,14 +24,28 @@ __device__ __forceinline__ SiteNb site_nb(const DomainDev& d, long long s, int& 
     const long long r = s - (long long)z * nxy;
     y = (int)(r / d.nx);
     x = (int)(r - (long long)y * d.nx);
+    // periodic wrap, or reflection at a wall (the image of the node beyond
+    // a wall is the node on the other side of it)
+    const bool wx = d.bc & LBPF_BC_WALL_X, wy = d.bc & LBPF_BC_WALL_Y, wz = d.bc & LBPF_BC_WALL_Z;
     SiteNb nb;
-    nb.oxm = (x == 0) ? d.nx - 1 : -1;
-    nb.oxp = (x == d.nx - 1) ? -(d.nx - 1) : 1;
-    nb.oym = (long long)((y == 0) ? d.ny - 1 : -1) * d.nx;
-    nb.oyp = (long long)((y == d.ny - 1) ? -(d.ny - 1) : 1) * d.nx;
-    nb.ozm = (d.nz == 1) ? 0 : (long long)((z == 0) ? d.nz - 1 : -1) * nxy;
-    nb.ozp = (d.nz == 1) ? 0 : (long long)((z == d.nz - 1) ? -(d.nz - 1) : 1) * nxy;
+    nb.oxm = (x == 0) ? (wx ? 1 : d.nx - 1) : -1;
+    nb.oxp = (x == d.nx - 1) ? (wx ? -1 : -(d.nx - 1)) : 1;
+    nb.oym = (long long)((y == 0) ? (wy ? 1 : d.ny - 1) : -1) * d.nx;
+    nb.oyp = (long long)((y == d.ny - 1) ? (wy ? -1 : -(d.ny - 1)) : 1) * d.nx;
+    nb.ozm = (d.nz == 1) ? 0 : (long long)((z == 0) ? (wz ? 1 : d.nz - 1) : -1) * nxy;
+    nb.ozp = (d.nz == 1) ? 0 : (long long)((z == d.nz - 1) ? (wz ? -1 : -(d.nz - 1)) : 1) * nxy;
     return nb;
+}
+
+// Mask of the walled axes along which the source (x, y, z) - e lies beyond a
+// wall of domain d.
+__device__ __forceinline__ int beyond_walls(const DomainDev& d, int x, int y, int z, int ex, int ey, int ez)
+{
+    int m = 0;
+    if ((d.bc & LBPF_BC_WALL_X) && ((x == 0 && ex > 0) || (x == d.nx - 1 && ex < 0))) m |= 1;
+    if ((d.bc & LBPF_BC_WALL_Y) && ((y == 0 && ey > 0) || (y == d.ny - 1 && ey < 0))) m |= 2;
+    if ((d.bc & LBPF_BC_WALL_Z) && d.nz > 1 && ((z == 0 && ez > 0) || (z == d.nz - 1 && ez < 0))) m |= 4;
+    return m;
 }
 
 // Gradient of phi at site s in lattice units (Sec. 4.2), global-memory stencil.
@@ -153,6 +167,22 @@ __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acu
             fv[j] = fj;
             u += fj;
         }
+        if (d.bc) {  // heat populations from beyond a wall: mirrored partners
+            R fw[UL::Q];
+            u = 0;
+#pragma unroll
+            for (int j = 0; j < UL::Q; ++j) {
+                const int m = beyond_walls(d, x, y, z, UL::ex(j), UL::ey(j), UL::ez(j));
+                R v = fv[j];
+#pragma unroll
+                for (int mm = 1; mm < 8; ++mm)
+                    if (m == mm) v = fv[reflect_dir<UL>(j, mm)];
+                fw[j] = v;
+                u += v;
+            }
+#pragma unroll
+            for (int j = 0; j < UL::Q; ++j) fv[j] = fw[j];
+        }
         if (!S::dev) {
 #pragma unroll
             for (int j = 0; j < UL::Q; ++j) fn[(long long)j * n + s] = from_real<T, R>(fv[j]);
@@ -257,18 +287,19 @@ struct LauncherImpl {
     using KU = KernelLattice<UL>;
     template <int V> static constexpr int TXV = tile_x(PL::D, V);
     template <int V> static constexpr int TYV = tile_y(PL::D, V);
-    template <int V> static constexpr auto kernel() { return step_kernel<KP, KU, S, TXV<V>, TYV<V>>; }
+    template <int V, bool W = false> static constexpr auto kernel() { return step_kernel<KP, KU, S, TXV<V>, TYV<V>, W>; }
     template <int V> static constexpr size_t smem_v() { return step_smem_bytes<KP, KU, S, TXV<V>, TYV<V>>(); }
 
-    template <int V>
+    template <int V, bool W>
     static cudaError_t step_v(const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        kernel<V>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V>(), s>>>(a);
+        kernel<V, W>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V>(), s>>>(a);
         return cudaGetLastError();
     }
-    static cudaError_t step(int v, const StepArgs& a, int n_blocks, cudaStream_t s)
+    static cudaError_t step(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        return v == 0 ? step_v<0>(a, n_blocks, s) : step_v<1>(a, n_blocks, s);
+        if (walls) return v == 0 ? step_v<0, true>(a, n_blocks, s) : step_v<1, true>(a, n_blocks, s);
+        return v == 0 ? step_v<0, false>(a, n_blocks, s) : step_v<1, false>(a, n_blocks, s);
     }
     static size_t smem(int v) { return v == 0 ? smem_v<0>() : smem_v<1>(); }
     static cudaError_t prepare(int v)
@@ -281,6 +312,11 @@ struct LauncherImpl {
                 if (e != cudaSuccess) return e;
             }
         }
+        cudaError_t e = v == 0 ? cudaFuncSetAttribute(kernel<0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)smem_v<0>())
+                               : cudaFuncSetAttribute(kernel<1, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)smem_v<1>());
+        if (e != cudaSuccess) return e;
         return v == 0 ? cudaFuncSetAttribute(kernel<0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<0>())
                       : cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
     }

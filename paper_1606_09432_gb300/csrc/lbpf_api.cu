@@ -44,6 +44,7 @@ struct lbpf_ctx {
     int n_items = 0, n_blocks = 0, items_cap = 0;
     int tile_v = 0, seg_len = 0, sms = 1;
     bool staged = false;  // step kernel with bulk-copy staging (staged_kernel.cuh)
+    int walls = 0;        // some domain has zero-flux walls: the step kernel's wall variant
     // graphs of kGraphSteps steady-state launches, keyed by (cur, fcur, acur)
     cudaGraphExec_t graphs[8] = {};
     bool graphs_off = false;
@@ -254,7 +255,7 @@ static double time_schedule(lbpf_ctx* c, int launches)
         if (cudaMemsetAsync(c->d_counters + c->cur, 0, sizeof(int), c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
         if ((c->staged ? c->L->step_staged(a, c->n_blocks, c->stream)
-                       : c->L->step(c->tile_v, a, c->n_blocks, c->stream)) != cudaSuccess)
+                       : c->L->step(c->tile_v, c->walls, a, c->n_blocks, c->stream)) != cudaSuccess)
             break;
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
@@ -349,6 +350,12 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         if (d.nx < 2 || d.ny < 2 || (dim == 2 && d.nz != 1) || (dim == 3 && d.nz < 2))
             return fail(nullptr, LBPF_EINVAL, "domain %d: sizes %d x %d x %d invalid for a %dD lattice (each >= 2; nz = 1 in 2D)",
                         k, d.nx, d.ny, d.nz, dim);
+        if (d.bc < 0 || d.bc > 7 || (dim == 2 && (d.bc & LBPF_BC_WALL_Z)) ||
+            ((d.bc & LBPF_BC_WALL_X) && d.nx < 3) || ((d.bc & LBPF_BC_WALL_Y) && d.ny < 3) ||
+            ((d.bc & LBPF_BC_WALL_Z) && d.nz < 3))
+            return fail(nullptr, LBPF_EINVAL,
+                        "domain %d: bc %d invalid (LBPF_BC_WALL_* bits, no z wall in 2D, >= 3 sites on a walled axis)",
+                        k, d.bc);
         if ((long long)d.nx * d.ny > (1LL << 31) || (long long)d.nx * d.ny * d.nz > (1LL << 40))
             return fail(nullptr, LBPF_EINVAL, "domain %d: too many sites", k);
         if (!finite_pos(d.dx) || !finite_pos(d.dt) || !finite_pos(d.W0) || !finite_pos(d.tau0) || !finite_pos(d.kappa))
@@ -402,6 +409,8 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         h.nx = d.nx;
         h.ny = d.ny;
         h.nz = d.nz;
+        h.bc = d.bc;
+        if (d.bc) c->walls = 1;
         h.n = (long long)d.nx * d.ny * d.nz;
         max_n = h.n > max_n ? h.n : max_n;
         // D_phi = (W0^2/tau0)(dt/dx^2), Eq. (LBE_RelaxationTime)
@@ -444,7 +453,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         const char* kenv = getenv("LBPF_KERNEL");
         c->staged = L->step_staged != nullptr && kenv && strcmp(kenv, "staged") == 0;
         for (const DomainDev& h : c->dd)
-            if (h.nx % 8 != 0 || h.nx < 64 || h.use_index) c->staged = false;
+            if (h.nx % 8 != 0 || h.nx < 64 || h.use_index || h.bc) c->staged = false;
         if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
             c->sms = 1;
         for (int v = 0; v < kNumTileVariants && rc == LBPF_OK; ++v) {
@@ -592,7 +601,7 @@ static int launch_step(lbpf_ctx* c)
     if (c->staged)
         CK(c->L->step_staged(a, c->n_blocks, c->stream));
     else
-        CK(c->L->step(c->tile_v, a, c->n_blocks, c->stream));
+        CK(c->L->step(c->tile_v, c->walls, a, c->n_blocks, c->stream));
     c->cur ^= 1;
     c->acur ^= 1;
     if (c->lagged) c->fcur ^= 1;
@@ -758,8 +767,9 @@ extern "C" int lbpf_measure(lbpf_ctx* c, int domain, int cx, int cy, int cz, dou
     if ((rc = sync_state(c))) return rc;
     CK(c->L->read_u(c->d_dd + domain, c->cur, c->fcur, c->acur, c->scratch, c->stream));
     double* outp = c->red + 3 * kReduceBlocks;
-    CK(launch_reduce(h.phi[c->cur], c->scratch, h.n, c->precision, c->red, outp, c->stream));
-    CK(launch_tips(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, c->dim, c->precision, outp + 3, c->stream));
+    CK(launch_reduce(h.phi[c->cur], c->scratch, h.n, c->precision, c->red, outp, c->stream, h.nx, h.ny, h.nz, h.bc,
+                     c->dim));
+    CK(launch_tips(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, c->dim, c->precision, outp + 3, c->stream, h.bc));
     {
         const int slot = (c->hist_last[domain] + 1) % kHistCap;
         CK(launch_hist_append(outp + 3, (double)c->steps * c->in[domain].dt,
@@ -804,7 +814,8 @@ extern "C" int lbpf_tip_radius(lbpf_ctx* c, int domain, int cx, int cy, int cz, 
     if (cx < 0 || cx >= h.nx || cy < 0 || cy >= h.ny || cz < 0 || cz >= h.nz)
         return fail(c, LBPF_EINVAL, "lbpf_tip_radius: centre outside the domain");
     double* out = c->red + 3 * kReduceBlocks + 15;
-    CK(launch_tip_radius(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, dir, J, c->dim, c->precision, out, c->stream));
+    CK(launch_tip_radius(h.phi[c->cur], h.nx, h.ny, h.nz, cx, cy, cz, dir, J, c->dim, c->precision, out, c->stream,
+                         h.bc));
     CK(cudaMemcpyAsync(rho, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBPF_OK;

@@ -32,9 +32,10 @@ __global__ void seed_kernel(const DomainDev* dp, long long n, int cur, int acur,
         int bestc = 0;
         for (int j = 0; j < ns; ++j) {
             const double* sd = seeds + 5 * j;
-            const double ddx = periodic_delta(x - sd[0], d.nx);
-            const double ddy = periodic_delta(y - sd[1], d.ny);
-            const double ddz = dim == 3 ? periodic_delta(z - sd[2], d.nz) : 0.0;
+            // minimum image along periodic axes, plain distance along walled ones
+            const double ddx = (d.bc & LBPF_BC_WALL_X) ? x - sd[0] : periodic_delta(x - sd[0], d.nx);
+            const double ddy = (d.bc & LBPF_BC_WALL_Y) ? y - sd[1] : periodic_delta(y - sd[1], d.ny);
+            const double ddz = dim == 3 ? ((d.bc & LBPF_BC_WALL_Z) ? z - sd[2] : periodic_delta(z - sd[2], d.nz)) : 0.0;
             const double v = tanh((sd[3] - sqrt(ddx * ddx + ddy * ddy + ddz * ddz)) * k);
             if (v > best) {
                 best = v;
@@ -67,19 +68,31 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Per-block FP64 partial sums of (1 + phi)/2 and (u - phi/2) and a count of
 // non-finite values, in a fixed order per block (deterministic).
+// With walls (bc != 0), (u - phi/2) of a site on a wall counts 1/2 per walled
+// coordinate at a wall: the site lies on a mirror plane (trapezoid rule).
 template <class R>
 __global__ void __launch_bounds__(256) reduce_kernel(const R* __restrict__ phi, const R* __restrict__ u, long long n,
-                                                     double* partial)
+                                                     double* partial, int nx, int ny, int nz, int bc, int dim)
 {
     double sf = 0.0, cs = 0.0, bad = 0.0;
+    const long long nxy = (long long)nx * ny;
     for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
         const double p = (double)phi[s], v = (double)u[s];
         if (!isfinite(p) || !isfinite(v)) {
             bad += 1.0;
             continue;
         }
+        double wgt = 1.0;
+        if (bc) {
+            const int z = (int)(s / nxy);
+            const long long r = s - (long long)z * nxy;
+            const int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
+            if ((bc & LBPF_BC_WALL_X) && (x == 0 || x == nx - 1)) wgt *= 0.5;
+            if ((bc & LBPF_BC_WALL_Y) && (y == 0 || y == ny - 1)) wgt *= 0.5;
+            if ((bc & LBPF_BC_WALL_Z) && dim == 3 && (z == 0 || z == nz - 1)) wgt *= 0.5;
+        }
         sf += 0.5 * (1.0 + p);
-        cs += v - 0.5 * p;
+        cs += wgt * (v - 0.5 * p);
     }
     __shared__ double red[3][8];
     sf = warp_sum(sf);
@@ -109,14 +122,17 @@ __global__ void reduce_finish_kernel(const double* partial, int nblocks, double*
 }
 
 cudaError_t launch_reduce(const void* phi, const void* u, long long n, int precision, double* partial, double* out,
-                          cudaStream_t s)
+                          cudaStream_t s, int nx, int ny, int nz, int bc, int dim)
 {
+    if (bc && (long long)nx * ny * nz != n) return cudaErrorInvalidValue;
     if (precision == LBPF_FP64)
         reduce_kernel<double><<<kReduceBlocks, 256, 0, s>>>(static_cast<const double*>(phi),
-                                                           static_cast<const double*>(u), n, partial);
+                                                           static_cast<const double*>(u), n, partial, nx, ny, nz, bc,
+                                                           dim);
     else
         reduce_kernel<float><<<kReduceBlocks, 256, 0, s>>>(static_cast<const float*>(phi),
-                                                          static_cast<const float*>(u), n, partial);
+                                                          static_cast<const float*>(u), n, partial, nx, ny, nz, bc,
+                                                          dim);
     reduce_finish_kernel<<<1, 32, 0, s>>>(partial, kReduceBlocks, out);
     return cudaGetLastError();
 }
@@ -124,9 +140,10 @@ cudaError_t launch_reduce(const void* phi, const void* u, long long n, int preci
 // Tip crossings: warp w scans the ray of axis w/2, sign +1 (even w) or -1,
 // k = 0 .. len-1 with len = half the domain length along the axis; the
 // outermost k with phi_k >= 0 > phi_{k+1} gives k + phi_k / (phi_k - phi_{k+1}).
+// A walled axis: the ray runs from the centre to the wall, without wrap.
 template <class R>
 __global__ void tips_kernel(const R* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz, int dim,
-                            double* out)
+                            double* out, int bc)
 {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int axis = w >> 1, sign = (w & 1) ? -1 : 1;
@@ -136,7 +153,8 @@ __global__ void tips_kernel(const R* __restrict__ phi, int nx, int ny, int nz, i
         return;
     }
     const int nax = axis == 0 ? nx : (axis == 1 ? ny : nz);
-    const int len = nax / 2;
+    const int cax = axis == 0 ? cx : (axis == 1 ? cy : cz);
+    const int len = (bc >> axis) & 1 ? (sign > 0 ? nax - 1 - cax : cax) : nax / 2;
     auto at = [&](int k) -> double {
         int c[3] = {cx, cy, cz};
         c[axis] += sign * k;
@@ -163,12 +181,12 @@ __global__ void tips_kernel(const R* __restrict__ phi, int nx, int ny, int nz, i
 }
 
 cudaError_t launch_tips(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dim, int precision,
-                        double* out, cudaStream_t s)
+                        double* out, cudaStream_t s, int bc)
 {
     if (precision == LBPF_FP64)
-        tips_kernel<double><<<1, 192, 0, s>>>(static_cast<const double*>(phi), nx, ny, nz, cx, cy, cz, dim, out);
+        tips_kernel<double><<<1, 192, 0, s>>>(static_cast<const double*>(phi), nx, ny, nz, cx, cy, cz, dim, out, bc);
     else
-        tips_kernel<float><<<1, 192, 0, s>>>(static_cast<const float*>(phi), nx, ny, nz, cx, cy, cz, dim, out);
+        tips_kernel<float><<<1, 192, 0, s>>>(static_cast<const float*>(phi), nx, ny, nz, cx, cy, cz, dim, out, bc);
     return cudaGetLastError();
 }
 
@@ -283,8 +301,10 @@ cudaError_t launch_tip_velocity(const double* hist, int cap, int last, int count
 // crossing; thread 0 then fits x_c(j) = a + b j^2 per transverse plane in FP64
 // and returns the mean of -1/(2b) over the planes (-1 when no fit).
 template <class R>
+// Walled axes: transverse offsets beyond a wall are reflected (the mirror
+// image of the crystal) and the ray runs to the wall.
 __global__ void tip_radius_kernel(const R* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir,
-                                  int J, int dim, double* out)
+                                  int J, int dim, double* out, int bc)
 {
     __shared__ double xc[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -301,8 +321,14 @@ __global__ void tip_radius_kernel(const R* __restrict__ phi, int nx, int ny, int
                 ++cnt;
             }
         int c[3] = {cx, cy, cz};
-        c[tr] = ((c[tr] + j) % nn[tr] + nn[tr]) % nn[tr];
-        const int len = nn[axis] / 2;
+        if ((bc >> tr) & 1) {  // repeated reflection: |j| may exceed the domain
+            int v = c[tr] + j;
+            while (v < 0 || v > nn[tr] - 1) v = v < 0 ? -v : 2 * (nn[tr] - 1) - v;
+            c[tr] = v;
+        } else {
+            c[tr] = ((c[tr] + j) % nn[tr] + nn[tr]) % nn[tr];
+        }
+        const int len = (bc >> axis) & 1 ? (sign > 0 ? nn[axis] - 1 - c[axis] : c[axis]) : nn[axis] / 2;
         auto at = [&](int k) -> double {
             int p[3] = {c[0], c[1], c[2]};
             p[axis] = ((c[axis] + sign * k) % nn[axis] + nn[axis]) % nn[axis];
@@ -350,15 +376,15 @@ __global__ void tip_radius_kernel(const R* __restrict__ phi, int nx, int ny, int
 }
 
 cudaError_t launch_tip_radius(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir, int J, int dim,
-                              int precision, double* out, cudaStream_t s)
+                              int precision, double* out, cudaStream_t s, int bc)
 {
     const int threads = 32 * (2 * J + 1) * (dim - 1);
     if (precision == LBPF_FP64)
         tip_radius_kernel<double><<<1, threads, 0, s>>>(static_cast<const double*>(phi), nx, ny, nz, cx, cy, cz, dir,
-                                                         J, dim, out);
+                                                         J, dim, out, bc);
     else
         tip_radius_kernel<float><<<1, threads, 0, s>>>(static_cast<const float*>(phi), nx, ny, nz, cx, cy, cz, dir, J,
-                                                        dim, out);
+                                                        dim, out, bc);
     return cudaGetLastError();
 }
 

@@ -196,7 +196,8 @@ struct CrystalDev {
 };
 
 struct DomainDev {
-    int nx, ny, nz, pad0;
+    int nx, ny, nz;
+    int bc;             // LBPF_BC_WALL_* bits (0: periodic)
     long long n;        // sites
     double Dphi;        // (W0^2 / tau0) (dt / dx^2), Eq. (LBE_RelaxationTime)
     double qphi;        // dt / tau0, source factor of Eq. (LBE_Eq_Phase)
@@ -262,6 +263,24 @@ template <class L, class = void> struct IsXZ { static constexpr bool value = fal
 template <class L> struct IsXZ<L, decltype(void(L::xz))> { static constexpr bool value = L::xz; };
 // Lattice the step kernel is instantiated with.
 template <class L> using KernelLattice = typename std::conditional<L::D == 2, XZ<L>, L>::type;
+
+// Index of the direction of lattice L whose velocity is e_i with the
+// components of the axes in mask (bit 0 x, 1 y, 2 z) reversed: the mirror
+// image of e_i in walls normal to those axes.
+template <class L>
+LBPF_HD constexpr int reflect_dir(int i, int mask)
+{
+    const int tx = (mask & 1) ? -L::ex(i) : L::ex(i);
+    const int ty = (mask & 2) ? -L::ey(i) : L::ey(i);
+    const int tz = (mask & 4) ? -L::ez(i) : L::ez(i);
+    for (int j = 0; j < L::Q; ++j)
+        if (L::ex(j) == tx && L::ey(j) == ty && L::ez(j) == tz) return j;
+    return -1;
+}
+
+// Walls are mirror planes through the boundary nodes: index -k maps to k and
+// n - 1 + k to n - 1 - k (n >= 3 for the offsets of at most 2 used here).
+LBPF_HD int reflect_index(int v, int n) { return v < 0 ? -v : (v >= n ? 2 * (n - 1) - v : v); }
 
 // Index of the direction opposite to i on lattice L.
 template <class L>
@@ -365,11 +384,12 @@ __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz
 // Launchers exported by the per-lattice translation units.
 // ---------------------------------------------------------------------------
 struct Launchers {
-    // Fused step over all work items, tile variant v (rows kTileRows[v]).
-    cudaError_t (*step)(int v, const StepArgs& a, int n_blocks, cudaStream_t s);
+    // Fused step over all work items, tile variant v (rows kTileRows[v]);
+    // walls != 0 selects the variant that handles zero-flux walls.
+    cudaError_t (*step)(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s);
     // Dynamic shared memory of variant v.
     size_t (*step_smem)(int v);
-    // Opt variant v into its dynamic shared memory.
+    // Opt variant v (both wall variants) into its dynamic shared memory.
     cudaError_t (*prepare)(int v);
     // Resident blocks per SM of variant v.
     int (*blocks_per_sm)(int v);
@@ -409,11 +429,14 @@ cudaError_t launch_seed(const DomainDev* d, long long n, int cur, int acur, int 
 // out[2] = number of non-finite phi or u values; partial[] holds one pair of
 // FP64 partial sums and a count per block (scratch of 3 * kReduceBlocks).
 constexpr int kReduceBlocks = 304;
+// With walls (bc != 0) the u - phi/2 sum weights nodes on a wall by 1/2 per
+// walled coordinate (they lie on the mirror planes).
 cudaError_t launch_reduce(const void* phi, const void* u, long long n, int precision, double* partial, double* out,
-                          cudaStream_t s);
-// Tip crossings along +-x, +-y, +-z from (cx, cy, cz); out[6].
+                          cudaStream_t s, int nx = 0, int ny = 0, int nz = 0, int bc = 0, int dim = 3);
+// Tip crossings along +-x, +-y, +-z from (cx, cy, cz); out[6].  Rays cover
+// half the domain on periodic axes and run to the wall on walled ones.
 cudaError_t launch_tips(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dim, int precision,
-                        double* out, cudaStream_t s);
+                        double* out, cudaStream_t s, int bc = 0);
 // Measurement history (time, tip6) per domain and the FP64 tip fits.
 cudaError_t launch_hist_append(const double* tips6, double t, double* slot, cudaStream_t s);
 cudaError_t launch_tip_velocity(const double* hist, int cap, int last, int count, int window, double dx, double* out,
@@ -421,7 +444,7 @@ cudaError_t launch_tip_velocity(const double* hist, int cap, int last, int count
 // Tip radius of the tip along dir (0..5) from rays at transverse offsets
 // |j| <= J (J <= 7 in 3D, <= 15 in 2D); out[0].
 cudaError_t launch_tip_radius(const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int dir, int J, int dim,
-                              int precision, double* out, cudaStream_t s);
+                              int precision, double* out, cudaStream_t s, int bc = 0);
 // int8 <-> int32 index copies.
 cudaError_t launch_index_to_i32(const int8_t* in, int* out, long long n, cudaStream_t s);
 cudaError_t launch_index_from_i32(const int* in, int8_t* out, long long n, int n_crystals, cudaStream_t s);

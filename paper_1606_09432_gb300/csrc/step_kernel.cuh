@@ -100,7 +100,12 @@ template <> struct CoefIO<double> {
 };
 
 // One work item: the column (x0, y0) of one domain over planes [z0, z1).
-template <class PL, class UL, class S, int TXT, int TY>
+// WALLS: the domain may have zero-flux walls (mirror planes through the
+// boundary nodes, lbpf.h LBPF_BC_WALL_X): stencil indices beyond a wall are
+// reflected, and at a wall node every population whose source lies beyond
+// the wall takes the value of its mirrored partner (the bounce-back of Sec.
+// 3.3), for the phase-field and the heat populations alike.
+template <class PL, class UL, class S, int TXT, int TY, bool WALLS>
 __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
     static_assert(PL::D == 3 && UL::D == 3, "the step kernel marches along z (2D lattices through XZ)");
@@ -180,9 +185,32 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     const R xi2 = sizeof(R) == 4 ? R(fmax(dm.xi_lu, 1e-6) * fmax(dm.xi_lu, 1e-6)) : R(dm.xi_lu * dm.xi_lu);
     (void)Dphi;
 
-    auto wrapx = [&](int v) { return v < 0 ? v + nx : (v >= nx ? v - nx : v); };
-    auto wrapy = [&](int v) { return v < 0 ? v + ny : (v >= ny ? v - ny : v); };
-    auto wrapz = [&](int v) { return v < 0 ? v + nz : (v >= nz ? v - nz : v); };
+    // walled axes of the kernel's view (a 2D domain's y axis is the kernel's z)
+    const int bcm = WALLS ? dm.bc : 0;
+    const bool wX = (bcm & LBPF_BC_WALL_X) != 0;
+    const bool wY = !XZV && (bcm & LBPF_BC_WALL_Y) != 0;
+    const bool wZ = XZV ? (bcm & LBPF_BC_WALL_Y) != 0 : (bcm & LBPF_BC_WALL_Z) != 0;
+    auto wrapx = [&](int v) {
+        if (WALLS && wX) return reflect_index(v, nx);
+        return v < 0 ? v + nx : (v >= nx ? v - nx : v);
+    };
+    auto wrapy = [&](int v) {
+        if (WALLS && wY) return reflect_index(v, ny);
+        return v < 0 ? v + ny : (v >= ny ? v - ny : v);
+    };
+    auto wrapz = [&](int v) {
+        if (WALLS && wZ) return reflect_index(v, nz);
+        return v < 0 ? v + nz : (v >= nz ? v - nz : v);
+    };
+    // mask of the walled axes along which the source x - e of a site at
+    // (gx, gy, gz) inside the domain lies beyond a wall
+    auto beyond = [&](int gx, int gy, int gz, int ex, int ey, int ez) {
+        int m = 0;
+        if (wX && ((gx == 0 && ex > 0) || (gx == nx - 1 && ex < 0))) m |= 1;
+        if (wY && ((gy == 0 && ey > 0) || (gy == ny - 1 && ey < 0))) m |= 2;
+        if (wZ && ((gz == 0 && ez > 0) || (gz == nz - 1 && ez < 0))) m |= 4;
+        return m;
+    };
     auto sphi = [&](int zp) { return (zp + 2 * NPH) % NPH; };
     auto sh = [&](int zp) { return (zp + 2 * NH) % NH; };
     auto sco = [&](int zp) { return (zp + 3) % NC; };
@@ -367,6 +395,31 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     fv[j] = fj;
                     u += fj;
                 }
+                if constexpr (WALLS) {
+                    // a site inside the domain on a wall: heat populations
+                    // from beyond the wall are their mirrored partners
+                    // (frame sites beyond a wall are ghosts whose values are
+                    // never used; along periodic axes every frame site is real)
+                    const int gxu = x0 + lx - 1, gyu = y0 + ly - HC;
+                    const bool real = (!wX || (gxu >= 0 && gxu < nx)) && (!wY || (gyu >= 0 && gyu < ny)) &&
+                                      (!wZ || (zp >= 0 && zp < nz));
+                    if (bcm && real) {
+                        R fw[QU];
+                        u = 0;
+#pragma unroll
+                        for (int j = 0; j < QU; ++j) {
+                            const int m = beyond(gx, gy, zw, UL::ex(j), UL::ey(j), UL::ez(j));
+                            R v = fv[j];
+#pragma unroll
+                            for (int mm = 1; mm < 8; ++mm)
+                                if (m == mm) v = fv[reflect_dir<UL>(j, mm)];
+                            fw[j] = v;
+                            u += v;
+                        }
+#pragma unroll
+                        for (int j = 0; j < QU; ++j) fv[j] = fw[j];
+                    }
+                }
                 if (inner) {
                     if (!DEV) {
 #pragma unroll
@@ -517,6 +570,25 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             gnew[i] = v;
             phinew += v;
         }
+        if constexpr (WALLS) {
+            if (bcm) {
+                // populations whose source lies beyond a wall: mirrored partners
+                R gw[QG];
+                phinew = 0;
+#pragma unroll
+                for (int i = 0; i < QG; ++i) {
+                    const int m = beyond(gx, gy, z, PL::ex(i), PL::ey(i), PL::ez(i));
+                    R v = gnew[i];
+#pragma unroll
+                    for (int mm = 1; mm < 8; ++mm)
+                        if (m == mm) v = gnew[reflect_dir<PL>(i, mm)];
+                    gw[i] = v;
+                    phinew += v;
+                }
+#pragma unroll
+                for (int i = 0; i < QG; ++i) gnew[i] = gw[i];
+            }
+        }
         phin[s] = phinew;
         if (!DEV) {
 #pragma unroll
@@ -570,7 +642,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 // The launch uses counter[cur] and clears counter[cur ^ 1] for the next step
 // (launches on one stream run in order; cur alternates every step).
 // Launch bounds ask for 1024 resident threads per SM (64 registers a thread).
-template <class PL, class UL, class S, int TXT, int TY>
+template <class PL, class UL, class S, int TXT, int TY, bool WALLS>
 __global__ void __launch_bounds__(TXT * TY, 1024 / (TXT * TY)) step_kernel(const StepArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -586,7 +658,7 @@ __global__ void __launch_bounds__(TXT * TY, 1024 / (TXT * TY)) step_kernel(const
         __syncthreads();
         const int k = s_next;
         if (k >= args.n_items) break;
-        step_item<PL, UL, S, TXT, TY>(args, args.items[k], smem_raw);
+        step_item<PL, UL, S, TXT, TY, WALLS>(args, args.items[k], smem_raw);
         __syncthreads();
     }
 }

@@ -26,6 +26,7 @@ LBPF_READ_PHI, LBPF_READ_U, LBPF_READ_AS, LBPF_READ_INDEX = 1, 2, 4, 8
 (LBPF_Q_SITES, LBPF_Q_STEPS, LBPF_Q_BYTES_PER_SITE, LBPF_Q_DEVICE_BYTES, LBPF_Q_LAMBDA, LBPF_Q_STEP_KERNELS,
  LBPF_Q_TILE_ROWS, LBPF_Q_SEGMENT, LBPF_Q_BLOCKS, LBPF_Q_KERNEL) = range(10)
 LBPF_MAX_CRYSTALS = 16
+LBPF_BC_WALL_X, LBPF_BC_WALL_Y, LBPF_BC_WALL_Z = 1, 2, 4
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_fields", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
             "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius",
@@ -40,7 +41,7 @@ class lbpf_crystal(C.Structure):
 
 
 class lbpf_domain(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("W0", C.c_double), ("tau0", C.c_double),
                 ("kappa", C.c_double), ("lam", C.c_double), ("delta", C.c_double), ("xi", C.c_double),
                 ("n_crystals", C.c_int), ("crystals", lbpf_crystal * LBPF_MAX_CRYSTALS)]
@@ -120,10 +121,13 @@ def make_crystal(kind=LBPF_AS_CUBIC100, eps=0.0, gamma=0.0, q=4, phi0=0.0) -> lb
     return lbpf_crystal(kind, eps, gamma, q, phi0)
 
 
-def make_domain(nx, ny, nz=1, *, dx, dt, W0, tau0, kappa, lam=0.0, delta=0.0, xi=1e-7, crystals=None) -> lbpf_domain:
-    """lam <= 0 selects lambda* (the library applies Eq. (Kinetic-Coeff) with beta = 0)."""
+def make_domain(nx, ny, nz=1, *, dx, dt, W0, tau0, kappa, lam=0.0, delta=0.0, xi=1e-7, crystals=None,
+                bc=0) -> lbpf_domain:
+    """lam <= 0 selects lambda* (the library applies Eq. (Kinetic-Coeff) with
+    beta = 0); bc: LBPF_BC_WALL_* bits (0: periodic)."""
     d = lbpf_domain()
     d.nx, d.ny, d.nz = nx, ny, nz
+    d.bc = bc
     d.dx, d.dt, d.W0, d.tau0, d.kappa = dx, dt, W0, tau0, kappa
     d.lam = 0.0 if lam is None else lam
     d.delta, d.xi = delta, xi

@@ -36,6 +36,17 @@ def c3(n=512, eps=0.0, gamma=-0.02):
                 seeds=[(n // 2, n // 2, n // 2, 8.0, 0)], centre=(n // 2, n // 2, n // 2))
 
 
+def octant(n=351, eps=0.0, gamma=-0.02, delta=0.25, radius=8.0):
+    """The octant run of the paper's Sec. 5.3 (dendrite B): n^3 nodes with
+    zero-flux walls on all six faces (bc = 7), the seed at the origin on three
+    of them, the 3D parameter set of Sec. 5.2, the <110> form of Eq.
+    (As_MatSci) with (eps, gamma) = (0, -0.02), Delta = 0.25.  The paper does
+    not state the seed radius of its 3D runs; 8 sites as in the other 3D
+    configurations."""
+    return dict(shape=(n, n, n), params=dict(C3D_PARAMS, delta=delta), aniso=dict(kind=3, eps=eps, gamma=gamma),
+                seeds=[(0.0, 0.0, 0.0, radius, 0)], centre=(0, 0, 0), bc=7)
+
+
 class SplitMix64:
     """SplitMix64 generator (Steele, Lea, Flood 2014)."""
 

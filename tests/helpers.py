@@ -8,12 +8,12 @@ import numpy as np
 ORC_LAT = {0: 0, 1: 1, 2: 2, 3: 3}
 
 
-def oracle_run(O, lattice, shape, params, crystals, seeds=None, fields=None, grad=0, xi=1e-7):
+def oracle_run(O, lattice, shape, params, crystals, seeds=None, fields=None, grad=0, xi=1e-7, bc=0):
     nz, ny, nx = shape
     prm = dict(params)
     lam = prm.pop("lam", None)
     p = O.make_params(ORC_LAT[lattice], nx, ny, nz, grad=grad, lam=lam, xi=xi,
-                      crystals=[O.make_crystal(**c) for c in crystals], **prm)
+                      crystals=[O.make_crystal(**c) for c in crystals], bc=bc, **prm)
     o = O.Oracle(p)
     if seeds is not None:
         o.seed([list(s) for s in seeds])
@@ -23,12 +23,12 @@ def oracle_run(O, lattice, shape, params, crystals, seeds=None, fields=None, gra
 
 
 def gpu_run(L, lattice, shape, params, crystals, seeds=None, fields=None, grad=0, precision=None, xi=1e-7,
-            stream=None):
+            stream=None, bc=0):
     nz, ny, nx = shape
     prm = dict(params)
     lam = prm.pop("lam", None)
     dom = L.make_domain(nx, ny, nz, lam=0.0 if lam is None else lam, xi=xi,
-                        crystals=[L.make_crystal(**c) for c in crystals], **prm)
+                        crystals=[L.make_crystal(**c) for c in crystals], bc=bc, **prm)
     s = L.Solver(dom, lattice, grad, L.LBPF_FP64 if precision is None else precision, stream=stream)
     if seeds is not None:
         s.seed(seeds)
