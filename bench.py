@@ -357,6 +357,35 @@ def run_surrogate(args, size=1024):
     return 0
 
 
+def run_replicate(args):
+    """Paper-scale runs of Secs. 4.2 and 5.2 (paper_1606_09432_gb300.replicate):
+    one JSON line per run, with the paper's values as context."""
+    import torch
+    from paper_1606_09432_gb300 import build as B
+    B.build()
+    from paper_1606_09432_gb300 import lbpf as L
+    from paper_1606_09432_gb300 import replicate as R
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    paper42 = {"FD": {"err_l2": 1.71e-1, "rot60_max": 1.446, "rot60_min": -1.454},
+               "DD": {"err_l2": 3.04e-3, "rot60_max": 0.1, "rot60_min": -0.103}}
+    if args.replicate in ("sec42", "all"):
+        for grad in (L.LBPF_GRAD_FD, L.LBPF_GRAD_DD):
+            t0 = time.perf_counter()
+            r = R.sec42(L, grad, precision=L.LBPF_FP64, steps=args.rep_steps or 100000)
+            r.update(seconds=round(time.perf_counter() - t0, 1), precision="f64", paper=paper42[r["grad"]],
+                     experiment="Sec. 4.2 sixfold crystal 800^2, walls, q=6, eps=0.05, Delta=0.30")
+            print(json.dumps(r), flush=True)
+    if args.replicate in ("sec52", "all"):
+        for which in "ABC":
+            t0 = time.perf_counter()
+            r = R.sec52(L, which, precision=L.LBPF_FP32)
+            r.update(seconds=round(time.perf_counter() - t0, 1), precision="f32",
+                     experiment="Sec. 5.2 dendrite 351^3, walls, Delta=0.30, seed R=8 at the centre",
+                     paper="slices superimposed (Fig. 8)")
+            print(json.dumps(r), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +405,9 @@ def main():
     ap.add_argument("--sur-train", type=int, default=1500, help="Adam steps")
     ap.add_argument("--sur-train-size", type=int, default=128, help="side of the training domains")
     ap.add_argument("--sur-steps", type=int, default=4400, help="LB steps to solution of the timed run")
+    ap.add_argument("--replicate", choices=["sec42", "sec52", "all"],
+                    help="paper-scale isotropy runs of Secs. 4.2 / 5.2 instead of the benchmark")
+    ap.add_argument("--rep-steps", type=int, default=0, help="steps of the Sec. 4.2 run (default 1e5)")
     ap.add_argument("--surrogate", action="store_true",
                     help="time-to-solution of surrogate + LB vs plain LB (trains a network first)")
     args = ap.parse_args()
@@ -385,6 +417,8 @@ def main():
         return run_reference(args)
     if args.surrogate:
         return run_surrogate(args)
+    if args.replicate:
+        return run_replicate(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -27,9 +27,11 @@ def O():
     return oracle
 
 
-def test_batched_multicrystal_parity(L, O):
+@pytest.mark.parametrize("xi", [0.1, 1e-7])
+def test_batched_multicrystal_parity(L, O, xi):
     """Three ragged 2D domains, each with its own crystals and index field,
-    advanced by one launch per step, against one oracle run per domain."""
+    advanced by one launch per step, against one oracle run per domain; the
+    index threshold xi at 0.1 and at the paper's 1e-7 (Sec. 4.3)."""
     specs = [((1, 45, 70), [(15.0, 14.0, 0, 5.0, 0), (50.0, 30.0, 0, 6.0, 1)]),
              ((1, 64, 33), [(16.0, 20.0, 0, 4.0, 0), (16.0, 48.0, 0, 5.5, 1), (5.0, 5.0, 0, 4.0, 2)]),
              ((1, 40, 52), [(26.0, 20.0, 0, 6.0, 0)])]
@@ -39,9 +41,9 @@ def test_batched_multicrystal_parity(L, O):
     for k, (shape, seeds) in enumerate(specs):
         cr = [dict(kind=1, eps=0.03 + 0.01 * j, q=4 + j, phi0=0.2 * j + 0.1 * k) for j in range(len(seeds))]
         crys.append(cr)
-        doms.append(L.make_domain(shape[2], shape[1], 1, lam=lam, xi=0.1, crystals=[L.make_crystal(**c) for c in cr],
+        doms.append(L.make_domain(shape[2], shape[1], 1, lam=lam, xi=xi, crystals=[L.make_crystal(**c) for c in cr],
                                   **prm))
-        oracles.append(oracle_run(O, 0, shape, dict(prm, lam=lam), cr, seeds=seeds, xi=0.1))
+        oracles.append(oracle_run(O, 0, shape, dict(prm, lam=lam), cr, seeds=seeds, xi=xi))
     s = L.Solver(doms, 0, 0, L.LBPF_FP64)
     for k, (_, seeds) in enumerate(specs):
         s.seed(seeds, domain=k)

@@ -88,14 +88,17 @@ def test_fp64_2d_forms(L, O, form, grad):
     assert maxabs(phi, o.fields()[0]) <= 1e-10 and maxabs(u, o.fields()[1]) <= 1e-10
 
 
-def test_fp64_multicrystal_index(L, O):
+@pytest.mark.parametrize("xi", [1e-1, 1e-7])
+def test_fp64_multicrystal_index(L, O, xi):
+    """Three crystals and the index field of Sec. 4.3, at xi = 0.1 and at the
+    paper's xi = 1e-7 (physical units)."""
     shape = (1, 50, 70)
     prm = dict(W.C4_PARAMS, delta=0.35)
     crs = [dict(kind=1, eps=0.04, q=4, phi0=0.785), dict(kind=1, eps=0.04, q=5, phi0=0.087),
            dict(kind=1, eps=0.04, q=6, phi0=0.0)]
     seeds = [(15.0, 14.0, 0, 5.0, 0), (50.0, 18.0, 0, 6.0, 1), (35.0, 38.0, 0, 4.5, 2)]
-    o = oracle_run(O, 0, shape, prm, crs, seeds=seeds, xi=1e-1)
-    s = gpu_run(L, 0, shape, prm, crs, seeds=seeds, xi=1e-1)
+    o = oracle_run(O, 0, shape, prm, crs, seeds=seeds, xi=xi)
+    s = gpu_run(L, 0, shape, prm, crs, seeds=seeds, xi=xi)
     I0 = s.field(L.LBPF_FIELD_INDEX)
     assert np.array_equal(I0, o.fields()[2])
     for k in range(4):
@@ -108,8 +111,11 @@ def test_fp64_multicrystal_index(L, O):
               f"index mismatches {(gI != oI).sum()}")
         assert np.array_equal(gI, oI)
         assert maxabs(phi, ophi) <= 1e-10 and maxabs(u, ou) <= 1e-10
-    assert (oI == 0).any() and set(np.unique(oI)) == {0, 1, 2, 3}
-    assert (oI != I0).any()  # the index field spread
+    assert set(np.unique(oI)) >= {1, 2, 3}
+    if xi > 1e-3:
+        assert (oI == 0).any() and (oI != I0).any()  # the index field spread
+    else:  # the tanh tails exceed xi = 1e-7 everywhere: every site has a crystal
+        assert (oI != 0).all()
 
 
 @pytest.mark.parametrize("lattice", [0, 1])
@@ -215,6 +221,8 @@ def test_errors(L):
 
 
 def test_fp32_3d_vs_oracle(L, O):
+    """48^3 D3Q15/D3Q7 FP32 against the FP64 oracle: 1e-4 on phi and u and
+    tips within 0.5 at 250, 500, 750 and 1000 steps."""
     w = W.c2(48)
     cr = [w["aniso"]]
     o = oracle_run(O, 1, w["shape"], w["params"], cr, seeds=w["seeds"])
@@ -230,7 +238,8 @@ def test_fp32_3d_vs_oracle(L, O):
         errs.append((maxabs(phi, ophi), maxabs(u, ou), np.abs(tip - otip).max()))
         print(f"FP32 vs FP64 oracle after {250 * (k + 1)} steps: phi {errs[-1][0]:.2e}, u {errs[-1][1]:.2e}, "
               f"tips {errs[-1][2]:.2e} (tip {otip[0]:.3f})")
-    assert errs[1][0] <= 1e-4 and errs[1][1] <= 1e-4  # 500 steps
+    # the FP32 bar at every checkpoint through 1000 steps
+    assert max(e[0] for e in errs) <= 1e-4 and max(e[1] for e in errs) <= 1e-4
     assert max(e[2] for e in errs) <= 0.5
     assert otip[0] > 9.0  # grew
 
@@ -532,3 +541,50 @@ def test_read_fields_fp32_as(L, O):
     far = G > 1e-2  # the interface; FP32 rounding of phi moves a_s by ~1e-7 / |G|
     print(f"FP32 a_s vs oracle after 100 steps: {maxabs(a[far], oa[far]):.2e} where |G| > 1e-2")
     assert far.sum() > 1000 and maxabs(a[far], oa[far]) <= 1e-4
+
+
+def test_512_schedule_parity(L, O):
+    """The work schedule of the 512^3 workload (tiles of 32 x 8, z-segments of
+    66 planes) on a domain the oracle holds, 64 x 64 x 200, FP64 against the
+    oracle (1e-10), so that multi-segment columns of that length are checked
+    against the method itself."""
+    shape = (200, 64, 64)
+    w = W.c3(64, eps=0.02, gamma=-0.02)
+    seeds = [(32.0, 30.0, 100.0, 8.0, 0), (20.0, 40.0, 33.0, 6.0, 0), (40.0, 20.0, 166.0, 6.0, 0)]
+    cr = [w["aniso"]]
+    o = oracle_run(O, 1, shape, w["params"], cr, seeds=seeds)
+    s = gpu_run(L, 1, shape, w["params"], cr, seeds=seeds)
+    L.lbpf_set_schedule(s.ctx, 8, 66)
+    assert s.query(L.LBPF_Q_SEGMENT) == 66 and s.query(L.LBPF_Q_TILE_ROWS) == 8
+    o.step(80)
+    s.step(80)
+    phi, u = s.fields()
+    assert maxabs(phi, o.fields()[0]) <= 1e-10 and maxabs(u, o.fields()[1]) <= 1e-10
+
+
+def test_full_size_512_invariants(L):
+    """512^3 D3Q15 FP16 deviations (the benchmark's configuration, schedule
+    and launch), 400 steps: the <110> crystal keeps the cubic symmetry of its
+    centred seed up to the 16-bit form's rounding (the six tips within 5e-2,
+    measured 9e-3; the core within 0.15, measured 6.9e-2: FP16 rounding of
+    mirrored sites differs, and the growth amplifies it), and sum(u - phi/2)
+    is conserved to 1e-5 (measured 6e-7)."""
+    w = W.c3(512, eps=0.0, gamma=-0.02)
+    s = gpu_run(L, 1, w["shape"], w["params"], [w["aniso"]], seeds=w["seeds"], precision=L.LBPF_FP32_FP16DEV)
+    tip0, _, c0 = s.measure(*w["centre"])
+    s.step(400)
+    tip, sf, c1 = s.measure(*w["centre"])
+    print(f"512^3 FP16 deviations, 400 steps: tips {tip}, conserved drift {abs(c1 - c0) / abs(c0):.2e}")
+    assert abs(c1 - c0) <= 1e-5 * abs(c0)
+    assert tip[0] > tip0[0] + 0.2
+    # FP16 rounding differs between mirrored sites (directions are summed in
+    # one fixed order), so the six arms agree to a few 1e-3 (measured 9e-3)
+    assert np.abs(tip - tip[0]).max() < 5e-2
+    phi = s.field(0)
+    c = 256
+    core = phi[c - 30:c + 31, c - 30:c + 31, c - 30:c + 31]
+    assert np.isfinite(core).all()
+    for t in (core[::-1], core.transpose(1, 0, 2), core.transpose(2, 1, 0), core[:, ::-1, :]):
+        d = maxabs(core, t)
+        print(f"512^3 FP16 core symmetry: {d:.2e}")
+        assert d < 0.15

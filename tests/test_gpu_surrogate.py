@@ -51,6 +51,48 @@ def test_forward_backward_match_oracle(env):
         off += n + co
 
 
+def test_forward_backward_elementwise(env):
+    """Element by element against the BF16-emulating oracle.  Both sides
+    round the convolution operands to BF16; they differ in accumulation
+    (FP32 on the tensor cores, FP64 in the oracle), which can move an
+    activation across a BF16 rounding boundary (one BF16 ulp, 2^-8
+    relative) or across a ReLU kink.  Bars, per element: the output within
+    1e-2 of the output's largest magnitude (measured: about 1e-3), each
+    layer's weight gradient within 5e-2 of that layer's largest gradient
+    magnitude, and 99 % of the output elements within 2e-3."""
+    torch, U, L, S, W = env
+    net = L.Net(32, 64, batch=2, seed=7)
+    p = net.params().astype(np.float64)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 32, 64, 5)).astype(np.float32)
+    x[..., 0] = np.tanh(x[..., 0])
+    y = torch.empty((2, 32, 64, 2), device="cuda")
+    net.forward(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    yo, cache = U.forward(p, x.astype(np.float64), emulate=True)
+    d = np.abs(y.cpu().numpy().astype(np.float64) - yo) / np.abs(yo).max()
+    print(f"forward: max {d.max():.2e}, 99% {np.quantile(d, 0.99):.2e}, median {np.median(d):.2e} "
+          "(relative to max |y|)")
+    assert d.max() <= 1e-2 and np.quantile(d, 0.99) <= 2e-3
+    dy = rng.standard_normal((2, 32, 64, 2)).astype(np.float32)
+    g = net.backward(torch.from_numpy(dy).cuda()).astype(np.float64)
+    go = U.backward(p, cache, dy.astype(np.float64), emulate=True)
+    off = 0
+    for li, (ci, co) in enumerate(U.LAYERS):
+        n = 9 * ci * co
+        gw, gwo = g[off:off + n], go[off:off + n]
+        e = np.abs(gw - gwo) / np.abs(gwo).max()
+        gb, gbo = g[off + n:off + n + co], go[off + n:off + n + co]
+        eb = np.abs(gb - gbo).max() / max(np.abs(gbo).max(), 1e-30)
+        print(f"layer {li} ({ci}->{co}): weight grad max {e.max():.2e}, 99% {np.quantile(e, 0.99):.2e}; "
+              f"bias grad max {eb:.2e}")
+        assert e.max() <= 5e-2 and eb <= 5e-2
+        off += n + co
+    hw = g[off:]
+    hwo = go[off:]
+    assert np.abs(hw - hwo).max() <= 2e-2 * np.abs(hwo).max()
+
+
 @pytest.mark.parametrize("alpha", [0.0, 20.0])
 def test_weighted_loss_matches_oracle(env, alpha):
     """The loss a training step reports (before its update) is the oracle's
