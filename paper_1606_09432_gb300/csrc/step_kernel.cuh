@@ -204,6 +204,11 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     };
     // mask of the walled axes along which the source x - e of a site at
     // (gx, gy, gz) inside the domain lies beyond a wall
+    // a site inside the domain on one of its walls
+    auto on_wall = [&](int gx, int gy, int gz) {
+        return (wX && (gx == 0 || gx == nx - 1)) || (wY && (gy == 0 || gy == ny - 1)) ||
+               (wZ && (gz == 0 || gz == nz - 1));
+    };
     auto beyond = [&](int gx, int gy, int gz, int ex, int ey, int ez) {
         int m = 0;
         if (wX && ((gx == 0 && ex > 0) || (gx == nx - 1 && ex < 0))) m |= 1;
@@ -403,7 +408,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     const int gxu = x0 + lx - 1, gyu = y0 + ly - HC;
                     const bool real = (!wX || (gxu >= 0 && gxu < nx)) && (!wY || (gyu >= 0 && gyu < ny)) &&
                                       (!wZ || (zp >= 0 && zp < nz));
-                    if (bcm && real) {
+                    if (bcm && real && on_wall(gx, gy, zw)) {
                         R fw[QU];
                         u = 0;
 #pragma unroll
@@ -571,7 +576,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             phinew += v;
         }
         if constexpr (WALLS) {
-            if (bcm) {
+            if (bcm && on_wall(gx, gy, z)) {
                 // populations whose source lies beyond a wall: mirrored partners
                 R gw[QG];
                 phinew = 0;
