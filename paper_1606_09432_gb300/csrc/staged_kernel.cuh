@@ -436,35 +436,32 @@ __device__ __forceinline__ void staged_item(const StepArgs& args, const WorkItem
         const int gt = (lty + 1) * GX + ltx + 8;  // g frame (x0-8, y0-1)
         const int cx = ltx + 1, cy = lty + 1;
         const R phy = s_phi[sphi(z) * RP + (lty + 2) * RX + ltx + 4];
-        R dl[QG];
-        R d0 = 0;
-#pragma unroll
-        for (int i = 1; i < QG; ++i) {
-            const int nsl = PL::ez(i) != 0 ? 3 : 2;
-            dl[i] = to_real(s_g[G::first_slot(i, GNZ, G::GSL) + ring(z, nsl) * G::GSL + gt]);
-            d0 -= dl[i];
-        }
-        dl[0] = d0;
+        // directions 1 .. Q-1, then the rest population (as in step_kernel)
         R gnew[QG];
-        R phinew = 0;
+        R phinew = 0, d0 = 0;
 #pragma unroll
-        for (int i = 0; i < QG; ++i) {
+        for (int k = 0; k < QG; ++k) {
+            const int i = (k + 1) % QG;
             const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
             R c1, c2, cs, vx, vy, vz;
             CoefIO<R>::load(s_co + sco(z - ez) * NCO * CP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
                             cs, vx, vy, vz);
-            R gp;
-            if (i == 0) {
-                gp = d0;
-            } else {
+            R gl, gp;
+            if (i > 0) {
                 const int nsl = ez != 0 ? 3 : 2;
-                gp = to_real(s_g[G::first_slot(i, GNZ, G::GSL) + ring(z - ez, nsl) * G::GSL + gt - ey * GX - ex]);
+                const int f0 = G::first_slot(i, GNZ, G::GSL);
+                const R d = to_real(s_g[f0 + ring(z, nsl) * G::GSL + gt]);
+                d0 -= d;
+                gl = R(PL::w(i)) * phy + d;
+                gp = to_real(s_g[f0 + ring(z - ez, nsl) * G::GSL + gt - ey * GX - ex]);
+            } else {
+                gl = R(PL::w(0)) * phy + d0;
+                gp = d0;
             }
             R ev = R(0);
             if (ex) ev += R(ex) * vx;
             if (ey) ev += R(ey) * vy;
             if (ez) ev += R(ez) * vz;
-            const R gl = R(PL::w(i)) * phy + dl[i];
             const R v = c1 * gp - c2 * gl + R(PL::w(i)) * (cs + ev);
             gnew[i] = v;
             phinew += v;

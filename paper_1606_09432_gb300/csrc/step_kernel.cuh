@@ -538,40 +538,39 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         };
         const int px = ltx + XO, py = lty + HL;  // phi frame
         const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
-        R gl[QG];
-        R d0 = 0;
-        if (!DEV) {
-#pragma unroll
-            for (int i = 0; i < QG; ++i) gl[i] = to_real(gc[(long long)i * n + s]);
-        } else {
-            const R phy = s_phi[sphi(z) * RP + py * RX + px];
-#pragma unroll
-            for (int i = 1; i < QG; ++i) {
-                const R d = to_real(gc[(long long)(i - 1) * n + s]);
-                d0 -= d;
-                gl[i] = R(PL::w(i)) * phy + d;
-            }
-            gl[0] = R(PL::w(0)) * phy + d0;
-        }
+        // Each local population is read in the direction loop, so that only
+        // the new populations stay live.  With deviation storage the rest
+        // population comes last: its deviation d0 = -sum of the others.
+        const R phy = DEV ? s_phi[sphi(z) * RP + py * RX + px] : R(0);
         R gnew[QG];
-        R phinew = 0;
+        R phinew = 0, d0 = 0;
 #pragma unroll
-        for (int i = 0; i < QG; ++i) {
+        for (int k = 0; k < QG; ++k) {
+            const int i = DEV ? (k + 1) % QG : k;
             const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
             R c1, c2, cs, vx, vy, vz;
             CoefIO<R>::load(s_co + sco(z - ez) * NCO * CP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
                             cs, vx, vy, vz);
-            R gp;  // full storage: g_i(x); deviation storage: d_i(x) (w_i phi(x) is in cs)
+            // gl: g_i(y) (the non-local term); gp: full storage g_i(x),
+            // deviation storage d_i(x) (w_i phi(x) is in cs)
+            R gl, gp;
             if (!DEV) {
-                gp = i == 0 ? gl[0] : to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
+                gl = to_real(gc[(long long)i * n + s]);
+                gp = i == 0 ? gl : to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
+            } else if (i > 0) {
+                const R d = to_real(gc[(long long)(i - 1) * n + s]);
+                d0 -= d;
+                gl = R(PL::w(i)) * phy + d;
+                gp = to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
             } else {
-                gp = i == 0 ? d0 : to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
+                gl = R(PL::w(0)) * phy + d0;
+                gp = d0;
             }
             R ev = R(0);
             if (ex) ev += R(ex) * vx;
             if (ey) ev += R(ey) * vy;
             if (D == 3 && ez) ev += R(ez) * vz;
-            const R v = c1 * gp - c2 * gl[i] + R(PL::w(i)) * (cs + ev);
+            const R v = c1 * gp - c2 * gl + R(PL::w(i)) * (cs + ev);
             gnew[i] = v;
             phinew += v;
         }
