@@ -324,9 +324,9 @@ typedef enum {
  * a tile along z (3D) or y (2D).  tile_rows is 8 or 16: in 3D the tile is 32
  * sites along x by tile_rows along y; in 2D it is one row of 16 * tile_rows
  * sites (128 or 256) along x.  segment (>= 1) is the number of z-planes (3D)
- * or y-rows (2D) per work item (the staged kernel, LBPF_Q_KERNEL = 1, takes
- * only tile_rows = 8).  Results do not depend on the schedule; only speed
- * does.  A performance knob with no counterpart in the paper.
+ * or y-rows (2D) per work item (tile_rows = 16 exists only for periodic
+ * domains and the generic kernel).  Results do not depend on the schedule;
+ * only speed does.  A performance knob with no counterpart in the paper.
  * Errors: LBPF_EINVAL. */
 int lbpf_set_schedule(lbpf_ctx* ctx, int tile_rows, int segment);
 

@@ -37,17 +37,6 @@ __device__ __forceinline__ SiteNb site_nb(const DomainDev& d, long long s, int& 
     return nb;
 }
 
-// Mask of the walled axes along which the source (x, y, z) - e lies beyond a
-// wall of domain d.
-__device__ __forceinline__ int beyond_walls(const DomainDev& d, int x, int y, int z, int ex, int ey, int ez)
-{
-    int m = 0;
-    if ((d.bc & LBPF_BC_WALL_X) && ((x == 0 && ex > 0) || (x == d.nx - 1 && ex < 0))) m |= 1;
-    if ((d.bc & LBPF_BC_WALL_Y) && ((y == 0 && ey > 0) || (y == d.ny - 1 && ey < 0))) m |= 2;
-    if ((d.bc & LBPF_BC_WALL_Z) && d.nz > 1 && ((z == 0 && ez > 0) || (z == d.nz - 1 && ez < 0))) m |= 4;
-    return m;
-}
-
 // Gradient of phi at site s in lattice units (Sec. 4.2), global-memory stencil.
 template <class PL, class R>
 __device__ __forceinline__ void site_gradient(const R* phi, long long s, const SiteNb& nb, int grad, R& Gx, R& Gy,
@@ -168,20 +157,17 @@ __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acu
             u += fj;
         }
         if (d.bc) {  // heat populations from beyond a wall: mirrored partners
-            R fw[UL::Q];
-            u = 0;
+            const int lo = ((d.bc & LBPF_BC_WALL_X) && x == 0 ? 1 : 0) | ((d.bc & LBPF_BC_WALL_Y) && y == 0 ? 2 : 0) |
+                           ((d.bc & LBPF_BC_WALL_Z) && d.nz > 1 && z == 0 ? 4 : 0);
+            const int hi = ((d.bc & LBPF_BC_WALL_X) && x == d.nx - 1 ? 1 : 0) |
+                           ((d.bc & LBPF_BC_WALL_Y) && y == d.ny - 1 ? 2 : 0) |
+                           ((d.bc & LBPF_BC_WALL_Z) && d.nz > 1 && z == d.nz - 1 ? 4 : 0);
+            if (lo | hi) {
+                mirror_refill<UL, R>(fv, lo, hi);
+                u = 0;
 #pragma unroll
-            for (int j = 0; j < UL::Q; ++j) {
-                const int m = beyond_walls(d, x, y, z, UL::ex(j), UL::ey(j), UL::ez(j));
-                R v = fv[j];
-#pragma unroll
-                for (int mm = 1; mm < 8; ++mm)
-                    if (m == mm) v = fv[reflect_dir<UL>(j, mm)];
-                fw[j] = v;
-                u += v;
+                for (int j = 0; j < UL::Q; ++j) u += fv[j];
             }
-#pragma unroll
-            for (int j = 0; j < UL::Q; ++j) fv[j] = fw[j];
         }
         if (!S::dev) {
 #pragma unroll
@@ -287,7 +273,11 @@ struct LauncherImpl {
     using KU = KernelLattice<UL>;
     template <int V> static constexpr int TXV = tile_x(PL::D, V);
     template <int V> static constexpr int TYV = tile_y(PL::D, V);
-    template <int V, bool W = false> static constexpr auto kernel() { return step_kernel<KP, KU, S, TXV<V>, TYV<V>, W>; }
+    template <int V, bool W = false>
+    static constexpr auto kernel()
+    {
+        return step_kernel<KP, KU, S, TXV<V>, TYV<V>, W>;
+    }
     template <int V> static constexpr size_t smem_v() { return step_smem_bytes<KP, KU, S, TXV<V>, TYV<V>>(); }
 
     template <int V, bool W>
@@ -296,10 +286,12 @@ struct LauncherImpl {
         kernel<V, W>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V>(), s>>>(a);
         return cudaGetLastError();
     }
+    // Tile variant 0 is built with and without walls; the 16-row variant 1
+    // only for periodic domains (the context selects it for nothing else).
     static cudaError_t step(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        if (walls) return v == 0 ? step_v<0, true>(a, n_blocks, s) : step_v<1, true>(a, n_blocks, s);
-        return v == 0 ? step_v<0, false>(a, n_blocks, s) : step_v<1, false>(a, n_blocks, s);
+        if (v == 1) return walls ? cudaErrorInvalidValue : step_v<1, false>(a, n_blocks, s);
+        return walls ? step_v<0, true>(a, n_blocks, s) : step_v<0, false>(a, n_blocks, s);
     }
     static size_t smem(int v) { return v == 0 ? smem_v<0>() : smem_v<1>(); }
     static cudaError_t prepare(int v)
@@ -312,13 +304,11 @@ struct LauncherImpl {
                 if (e != cudaSuccess) return e;
             }
         }
-        cudaError_t e = v == 0 ? cudaFuncSetAttribute(kernel<0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)smem_v<0>())
-                               : cudaFuncSetAttribute(kernel<1, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)smem_v<1>());
-        if (e != cudaSuccess) return e;
-        return v == 0 ? cudaFuncSetAttribute(kernel<0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<0>())
-                      : cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
+        const int b0 = (int)smem_v<0>();
+        if (v == 1) return cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
+        cudaError_t e = cudaFuncSetAttribute(kernel<0, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
+        return e == cudaSuccess ? cudaFuncSetAttribute(kernel<0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b0)
+                                : e;
     }
     // the staged kernel: 3D, 16-bit deviation storage, lattices whose staging
     // fits two blocks per SM (D3Q15, D3Q19)
@@ -392,20 +382,5 @@ struct LauncherImpl {
         return &L;
     }
 };
-
-template <int LAT>
-const Launchers* launchers_for(int precision)
-{
-    using PL = typename Pair<LAT>::P;
-    using UL = typename Pair<LAT>::U;
-    switch (precision) {
-    case LBPF_FP64: return LauncherImpl<PL, UL, StoreF64>::get();
-    case LBPF_FP32: return LauncherImpl<PL, UL, StoreF32>::get();
-    case LBPF_FP32_FP16DEV: return LauncherImpl<PL, UL, StoreF16>::get();
-    case LBPF_FP32_BF16DEV: return LauncherImpl<PL, UL, StoreB16>::get();
-    case LBPF_FP32_FP16DEV_SR: return LauncherImpl<PL, UL, StoreF16SR>::get();
-    default: return nullptr;
-    }
-}
 
 }  // namespace lbpf

@@ -103,16 +103,7 @@ static int dev_alloc(lbpf_ctx* c, void** p, size_t bytes)
     return LBPF_OK;
 }
 
-static const Launchers* pick(int lattice, int precision)
-{
-    switch (lattice) {
-    case LBPF_D2Q9_D2Q5: return launchers_d2q9(precision);
-    case LBPF_D3Q15_D3Q7: return launchers_d3q15(precision);
-    case LBPF_D3Q19_D3Q7: return launchers_d3q19(precision);
-    case LBPF_D3Q27_D3Q7: return launchers_d3q27(precision);
-    default: return nullptr;
-    }
-}
+static const Launchers* pick(int lattice, int precision) { return launchers_for_pair(lattice, precision); }
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
@@ -303,7 +294,7 @@ static int autotune(lbpf_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     double best_t = 1e30, rule_t = 1e30;
     int best_v = 0, best_seg = default_segment(c, 0);
-    for (int v = 0; v < (c->staged ? 1 : kNumTileVariants); ++v) {
+    for (int v = 0; v < (c->staged || c->walls ? 1 : kNumTileVariants); ++v) {
         const int L0 = default_segment(c, v);
         const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
         for (int j = 0; j < 3; ++j) {
@@ -829,7 +820,8 @@ extern "C" int lbpf_set_schedule(lbpf_ctx* c, int tile_rows, int segment)
     for (int k = 0; k < kNumTileVariants; ++k)
         if (kTileRows[k] == tile_rows) v = k;
     if (v < 0 || segment < 1) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: tile_rows must be 8 or 16, segment >= 1");
-    if (c->staged && v != 0) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: the staged kernel uses 8-row tiles");
+    if ((c->staged || c->walls) && v != 0)
+        return fail(c, LBPF_EINVAL, "lbpf_set_schedule: 16-row tiles exist only for periodic domains (generic kernel)");
     CK(cudaStreamSynchronize(c->stream));
     c->tune_pending = false;
     c->tuned = "set";

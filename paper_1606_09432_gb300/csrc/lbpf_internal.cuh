@@ -278,6 +278,31 @@ LBPF_HD constexpr int reflect_dir(int i, int mask)
     return -1;
 }
 
+// Values of the populations of a site on walls after the specular refill: a
+// population whose source lies beyond the wall of axis a takes the value of
+// its mirror image in that wall.  Applied axis by axis (x, then y, then z) as
+// a permutation with a predicate per direction; a population beyond two or
+// three walls (edges, corners) ends with the value of its image in all of
+// them, the composition of the single reflections.  lo / hi: the site lies on
+// the low / high wall of axis a (bit a).
+template <class L, class R>
+__device__ __forceinline__ void mirror_refill(R (&v)[L::Q], int lo, int hi)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(((lo | hi) >> a) & 1)) continue;
+        R t[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int e = a == 0 ? L::ex(i) : (a == 1 ? L::ey(i) : L::ez(i));
+            const bool beyond = (((lo >> a) & 1) && e > 0) || (((hi >> a) & 1) && e < 0);
+            t[i] = beyond ? v[reflect_dir<L>(i, 1 << a)] : v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) v[i] = t[i];
+    }
+}
+
 // Walls are mirror planes through the boundary nodes: index -k maps to k and
 // n - 1 + k to n - 1 - k (n >= 3 for the offsets of at most 2 used here).
 LBPF_HD int reflect_index(int v, int n) { return v < 0 ? -v : (v >= n ? 2 * (n - 1) - v : v); }
@@ -385,7 +410,8 @@ __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz
 // ---------------------------------------------------------------------------
 struct Launchers {
     // Fused step over all work items, tile variant v (rows kTileRows[v]);
-    // walls != 0 selects the variant that handles zero-flux walls.
+    // walls != 0 selects the variant that handles zero-flux walls (built for
+    // variant 0 only).
     cudaError_t (*step)(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s);
     // Dynamic shared memory of variant v.
     size_t (*step_smem)(int v);
@@ -415,10 +441,9 @@ struct Launchers {
     int Qphi, Qu, D;
 };
 
-const Launchers* launchers_d2q9(int precision);
-const Launchers* launchers_d3q15(int precision);
-const Launchers* launchers_d3q19(int precision);
-const Launchers* launchers_d3q27(int precision);
+// Launchers of a lattice pair (lbpf_lattice) and precision (lbpf_precision),
+// nullptr for an unknown pair or precision (lbpf_launchers.cu).
+const Launchers* launchers_for_pair(int lattice, int precision);
 
 // Precision-generic kernels (seeding, measurements, index copies), in lbpf_fields.cu.
 // Seeds: n_seeds rows (x, y, z, R, crystal) in device memory.  Writes phi[cur],

@@ -202,19 +202,17 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         if (WALLS && wZ) return reflect_index(v, nz);
         return v < 0 ? v + nz : (v >= nz ? v - nz : v);
     };
-    // mask of the walled axes along which the source x - e of a site at
-    // (gx, gy, gz) inside the domain lies beyond a wall
     // a site inside the domain on one of its walls
     auto on_wall = [&](int gx, int gy, int gz) {
         return (wX && (gx == 0 || gx == nx - 1)) || (wY && (gy == 0 || gy == ny - 1)) ||
                (wZ && (gz == 0 || gz == nz - 1));
     };
-    auto beyond = [&](int gx, int gy, int gz, int ex, int ey, int ez) {
-        int m = 0;
-        if (wX && ((gx == 0 && ex > 0) || (gx == nx - 1 && ex < 0))) m |= 1;
-        if (wY && ((gy == 0 && ey > 0) || (gy == ny - 1 && ey < 0))) m |= 2;
-        if (wZ && ((gz == 0 && ez > 0) || (gz == nz - 1 && ez < 0))) m |= 4;
-        return m;
+    // walls the site lies on, low and high end of each axis (bit = axis)
+    auto wall_lo = [&](int gx, int gy, int gz) {
+        return (wX && gx == 0 ? 1 : 0) | (wY && gy == 0 ? 2 : 0) | (wZ && gz == 0 ? 4 : 0);
+    };
+    auto wall_hi = [&](int gx, int gy, int gz) {
+        return (wX && gx == nx - 1 ? 1 : 0) | (wY && gy == ny - 1 ? 2 : 0) | (wZ && gz == nz - 1 ? 4 : 0);
     };
     auto sphi = [&](int zp) { return (zp + 2 * NPH) % NPH; };
     auto sh = [&](int zp) { return (zp + 2 * NH) % NH; };
@@ -409,20 +407,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     const bool real = (!wX || (gxu >= 0 && gxu < nx)) && (!wY || (gyu >= 0 && gyu < ny)) &&
                                       (!wZ || (zp >= 0 && zp < nz));
                     if (bcm && real && on_wall(gx, gy, zw)) {
-                        R fw[QU];
+                        mirror_refill<UL, R>(fv, wall_lo(gx, gy, zw), wall_hi(gx, gy, zw));
                         u = 0;
 #pragma unroll
-                        for (int j = 0; j < QU; ++j) {
-                            const int m = beyond(gx, gy, zw, UL::ex(j), UL::ey(j), UL::ez(j));
-                            R v = fv[j];
-#pragma unroll
-                            for (int mm = 1; mm < 8; ++mm)
-                                if (m == mm) v = fv[reflect_dir<UL>(j, mm)];
-                            fw[j] = v;
-                            u += v;
-                        }
-#pragma unroll
-                        for (int j = 0; j < QU; ++j) fv[j] = fw[j];
+                        for (int j = 0; j < QU; ++j) u += fv[j];
                     }
                 }
                 if (inner) {
@@ -577,20 +565,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         if constexpr (WALLS) {
             if (bcm && on_wall(gx, gy, z)) {
                 // populations whose source lies beyond a wall: mirrored partners
-                R gw[QG];
+                mirror_refill<PL, R>(gnew, wall_lo(gx, gy, z), wall_hi(gx, gy, z));
                 phinew = 0;
 #pragma unroll
-                for (int i = 0; i < QG; ++i) {
-                    const int m = beyond(gx, gy, z, PL::ex(i), PL::ey(i), PL::ez(i));
-                    R v = gnew[i];
-#pragma unroll
-                    for (int mm = 1; mm < 8; ++mm)
-                        if (m == mm) v = gnew[reflect_dir<PL>(i, mm)];
-                    gw[i] = v;
-                    phinew += v;
-                }
-#pragma unroll
-                for (int i = 0; i < QG; ++i) gnew[i] = gw[i];
+                for (int i = 0; i < QG; ++i) phinew += gnew[i];
             }
         }
         phin[s] = phinew;
