@@ -71,6 +71,9 @@ typedef struct {
     double dx, dt, W0, tau0, kappa, lambda, delta, xi;
     int n_crystals;
     orc_crystal crystals[ORC_MAXC];
+    /* Advective velocity v of the heat equation (physical units; 0: the
+     * pure diffusion of the paper's runs), see heat_equilibrium. */
+    double adv[3];
 } orc_params;
 
 typedef struct {
@@ -531,8 +534,20 @@ static double geq_phase(const orc_state* s, int i, double phi, const double N[3]
     return s->Lg.w[i] * (phi - eN / s->Lg.e2 * (p->dt / p->dx) * (p->W0 * p->W0 / p->tau0));
 }
 
+/* Temperature e.d.f., Eq. (EqFunction_Tempr), f_i^(0) = w_i u; with an
+ * advective velocity v the advection-diffusion form of Sec. 3.1,
+ * f_i^(0) = w_i u [1 + e^{-2} e_i . v dt / dx], whose moments are u,
+ * v u dt / dx and e^2 u I. */
+static double heat_equilibrium(const orc_state* s, int i, double u)
+{
+    const orc_params* p = &s->p;
+    const int* e = s->Lu.e[i];
+    const double ev = e[0] * p->adv[0] + e[1] * p->adv[1] + e[2] * p->adv[2];
+    return s->Lu.w[i] * u * (1.0 + ev / s->Lu.e2 * p->dt / p->dx);
+}
+
 /* Populations from given phi and u fields: g_i = g_i^(0)(phi, N) with N from
- * the gradient of phi, f_i = f_i^(0) = w_i u, Eq. (EqFunction_Tempr).
+ * the gradient of phi, f_i = f_i^(0) (heat_equilibrium).
  * Reading: the paper does not state how the populations are initialised;
  * equilibrium populations are taken, as in the algorithm of Sec. 3.1. */
 static void init_populations(orc_state* s)
@@ -546,7 +561,7 @@ static void init_populations(orc_state* s)
                 gradient_at(p, &s->Lg, s->phi, x, y, z, G);
                 site_anisotropy(s, s->I[k], G, &a, N);
                 for (int i = 0; i < s->Lg.Q; ++i) s->g[(long)i * s->n + k] = geq_phase(s, i, s->phi[k], N);
-                for (int i = 0; i < s->Lu.Q; ++i) s->f[(long)i * s->n + k] = s->Lu.w[i] * s->u[k];
+                for (int i = 0; i < s->Lu.Q; ++i) s->f[(long)i * s->n + k] = heat_equilibrium(s, i, s->u[k]);
             }
     s->steps = 0;
 }
@@ -748,7 +763,8 @@ static void step_once(orc_state* s)
     }
 
     /* (3) heat equation, Eq. (LBE_Eq_Temp) with f^(0) = w_i u,
-     * Eq. (EqFunction_Tempr), and Q_u = (1/2) d(phi)/dt, Eq. (Source_Tempr),
+     * Eq. (EqFunction_Tempr) (or its advective form, heat_equilibrium), and
+     * Q_u = (1/2) d(phi)/dt, Eq. (Source_Tempr),
      * the time derivative by the explicit Euler difference
      * (phi(t + dt) - phi(t)) / dt of the phase field just computed.
      * eta_u from Eq. (ThermalDiffusivity): kappa = e^2 (eta_u - 1/2) dx^2/dt. */
@@ -764,7 +780,7 @@ static void step_once(orc_state* s)
                     const int* e = Lu->e[i];
                     long kn = site(p, x + e[0], y + e[1], z + e[2]);
                     double fi = s->f[(long)i * n + k];
-                    double feq = Lu->w[i] * u;
+                    double feq = heat_equilibrium(s, i, u);
                     if (!outside_walls(p, x + e[0], y + e[1], z + e[2])) /* else it leaves the box */
                         s->fnew[(long)i * n + kn] = fi - (fi - feq) / eta_u + Lu->w[i] * Qu * p->dt;
                 }

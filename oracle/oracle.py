@@ -74,7 +74,7 @@ class Params(C.Structure):
                 ("dx", C.c_double), ("dt", C.c_double), ("W0", C.c_double),
                 ("tau0", C.c_double), ("kappa", C.c_double), ("lam", C.c_double),
                 ("delta", C.c_double), ("xi", C.c_double),
-                ("n_crystals", C.c_int), ("crystals", Crystal * MAXC)]
+                ("n_crystals", C.c_int), ("crystals", Crystal * MAXC), ("adv", C.c_double * 3)]
 
 
 _lib = None
@@ -132,12 +132,14 @@ def make_crystal(kind=AS_CUBIC100, eps=0.0, gamma=0.0, q=4, phi0=0.0) -> Crystal
 
 
 def make_params(lattice_pair, nx, ny, nz=1, *, grad=GRAD_DD, dx=1.0, dt=1.0, W0=1.0, tau0=1.0,
-                kappa=1.0, lam=None, delta=0.0, xi=1e-7, crystals=(None,), bc=0) -> Params:
+                kappa=1.0, lam=None, delta=0.0, xi=1e-7, crystals=(None,), bc=0, adv=(0.0, 0.0, 0.0)) -> Params:
     p = Params()
     p.lattice = lattice_pair
     p.grad = grad
     p.nx, p.ny, p.nz = nx, ny, nz
     p.bc = bc
+    for a in range(3):
+        p.adv[a] = float(adv[a])
     p.dx, p.dt, p.W0, p.tau0, p.kappa = dx, dt, W0, tau0, kappa
     p.lam = lambda_star(kappa, tau0, W0) if lam is None else lam
     p.delta = delta
