@@ -154,6 +154,19 @@ typedef struct {
                         everywhere; with several, the crystal-index field of
                         Sec. 4.3 / Eq. (As_Multi) selects it per site          */
     lbpf_crystal crystals[LBPF_MAX_CRYSTALS];
+    double adv[3];   /* uniform velocity v (physical units; all zero: pure
+                        diffusion, the paper's runs).  Non-zero selects the
+                        advection-diffusion form of the heat equilibrium
+                        (Sec. 3.1, the equilibrium of Eq. EqFunction_Tempr with
+                        a first-order velocity term):
+                            f_i^(0) = w_i u (1 + e_i . v dt / (e^2 dx)),
+                        whose first moment is u v dt / dx, so the recovered
+                        equation is du/dt + div(u v) = kappa lap(u) + Q_u.
+                        Only with full storage (LBPF_FP64, LBPF_FP32); 0 along
+                        a 2D lattice's z and along every walled axis (the
+                        velocity is tangential to the walls).  Stable for
+                        |v| dt / dx well below 1; the scheme adds a numerical
+                        diffusion of order |v|^2 dt.  EINVAL otherwise. */
 } lbpf_domain;
 
 /* A diffuse spherical (circular in 2D) nucleus, Eq. (Initial_Condition). */

@@ -63,8 +63,17 @@ __device__ __forceinline__ void site_gradient(const R* phi, long long s, const S
     }
 }
 
+// e_j . a of heat direction j for a domain with an advective equilibrium
+// (DomainDev::adv), zero otherwise.
+template <class UL>
+__device__ __forceinline__ double adv_dot(const DomainDev& d, int j)
+{
+    return d.advect ? UL::ex(j) * d.adv[0] + UL::ey(j) * d.adv[1] + UL::ez(j) * d.adv[2] : 0.0;
+}
+
 // Equilibrium populations from phi (phi[cur]) and u (held in aux[acur]):
-// g_i = g_i^(0)(phi, N), Eq. (Feq_Phase); f_i = w_i u, Eq. (EqFunction_Tempr).
+// g_i = g_i^(0)(phi, N), Eq. (Feq_Phase); f_i = w_i u, Eq. (EqFunction_Tempr),
+// or w_i u (1 + e_i . a) with an advective equilibrium.
 // finalize_index: the seeded index keeps its value only where phi > 0 or
 // |grad phi| > xi.  Leaves a synchronised state; aux becomes C = u - phi/2 in
 // deviation storage (full storage does not use aux in that state).
@@ -110,7 +119,7 @@ __global__ void equilibrate_kernel(const DomainDev* dp, int cur, int fcur, int a
 #pragma unroll
         for (int j = 0; j < UL::Q; ++j) {
             if (!S::dev)
-                f[(long long)j * n + s] = from_real<T, R>(R(UL::w(j)) * u);
+                f[(long long)j * n + s] = from_real<T, R>(R(UL::w(j)) * u * (R(1) + R(adv_dot<UL>(d, j))));
             else if (j > 0)
                 f[(long long)(j - 1) * n + s] = from_real<T, R>(R(0));
         }
@@ -119,8 +128,9 @@ __global__ void equilibrate_kernel(const DomainDev* dp, int cur, int fcur, int a
 }
 
 // Heat update of step n-1 alone (Eq. LBE_Eq_Temp), lagged -> synchronised:
-// reads f[fcur] (f^{n-1}), aux[acur], phi[cur] (phi^n); writes f[fcur^1]
-// (f^n) and, in deviation storage, aux[acur^1] = C^n.
+// reads f[fcur] (f^{n-1}), aux[acur], phi[cur] (phi^n) and, with an
+// advective equilibrium, U[acur]; writes f[fcur^1] (f^n) and, in deviation
+// storage, aux[acur^1] = C^n.
 template <class PL, class UL, class S>
 __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acur)
 {
@@ -133,6 +143,7 @@ __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acu
     R* auxn = static_cast<R*>(d.aux[acur ^ 1]);
     const T* fc = static_cast<const T*>(d.f[fcur]);
     T* fn = static_cast<T*>(d.f[fcur ^ 1]);
+    const R* Uc = static_cast<const R*>(d.U[acur]);
     const R om = R(1) - R(d.inv_eta_u);
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
@@ -149,9 +160,11 @@ __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acu
             const long long src = s + nb.off(-UL::ex(j), -UL::ey(j), -UL::ez(j));
             const R h = auxc[src] + R(0.5) * phi[src];
             R fj;
-            if (!S::dev)
+            if (!S::dev) {
                 fj = om * to_real(fc[(long long)j * n + src]) + R(UL::w(j)) * h;
-            else
+                if (d.advect && (UL::ex(j) | UL::ey(j) | UL::ez(j)))
+                    fj += R(UL::w(j)) * R(adv_dot<UL>(d, j)) * Uc[src];
+            } else
                 fj = R(UL::w(j)) * h + om * ((j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]));
             fv[j] = fj;
             u += fj;
@@ -273,25 +286,38 @@ struct LauncherImpl {
     using KU = KernelLattice<UL>;
     template <int V> static constexpr int TXV = tile_x(PL::D, V);
     template <int V> static constexpr int TYV = tile_y(PL::D, V);
-    template <int V, bool W = false>
+    // the advective kernel (full storage; tile variant 0, with walls)
+    static constexpr bool kAdv = !S::dev;
+    template <int V, bool W = false, bool A = false>
     static constexpr auto kernel()
     {
-        return step_kernel<KP, KU, S, TXV<V>, TYV<V>, W>;
+        return step_kernel<KP, KU, S, TXV<V>, TYV<V>, W, A>;
     }
-    template <int V> static constexpr size_t smem_v() { return step_smem_bytes<KP, KU, S, TXV<V>, TYV<V>>(); }
+    template <int V, bool A = false>
+    static constexpr size_t smem_v()
+    {
+        return step_smem_bytes<KP, KU, S, TXV<V>, TYV<V>, A>();
+    }
 
-    template <int V, bool W>
+    template <int V, bool W, bool A = false>
     static cudaError_t step_v(const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        kernel<V, W>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V>(), s>>>(a);
+        kernel<V, W, A>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V, A>(), s>>>(a);
         return cudaGetLastError();
     }
-    // Tile variant 0 is built with and without walls; the 16-row variant 1
-    // only for periodic domains (the context selects it for nothing else).
-    static cudaError_t step(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s)
+    // Tile variant 0 is built periodic, with walls and (full storage) with an
+    // advective equilibrium; the 16-row variant 1 only for periodic domains
+    // (the context selects it for nothing else).
+    static cudaError_t step(int v, int kind, const StepArgs& a, int n_blocks, cudaStream_t s)
     {
-        if (v == 1) return walls ? cudaErrorInvalidValue : step_v<1, false>(a, n_blocks, s);
-        return walls ? step_v<0, true>(a, n_blocks, s) : step_v<0, false>(a, n_blocks, s);
+        if (v == 1) return kind ? cudaErrorInvalidValue : step_v<1, false>(a, n_blocks, s);
+        if (kind & kStepAdvect) {
+            if constexpr (kAdv)
+                return step_v<0, true, true>(a, n_blocks, s);
+            else
+                return cudaErrorNotSupported;
+        }
+        return kind ? step_v<0, true>(a, n_blocks, s) : step_v<0, false>(a, n_blocks, s);
     }
     static size_t smem(int v) { return v == 0 ? smem_v<0>() : smem_v<1>(); }
     static cudaError_t prepare(int v)
@@ -307,8 +333,13 @@ struct LauncherImpl {
         const int b0 = (int)smem_v<0>();
         if (v == 1) return cudaFuncSetAttribute(kernel<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v<1>());
         cudaError_t e = cudaFuncSetAttribute(kernel<0, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
-        return e == cudaSuccess ? cudaFuncSetAttribute(kernel<0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b0)
-                                : e;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel<0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
+        if constexpr (kAdv) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kernel<0, true, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_v<0, true>());
+        }
+        return e;
     }
     // the staged kernel: 3D, 16-bit deviation storage, lattices whose staging
     // fits two blocks per SM (D3Q15, D3Q19)
@@ -334,11 +365,20 @@ struct LauncherImpl {
         }
         return nb > 0 ? nb : 1;
     }
-    static int blocks_per_sm(int v)
+    static int blocks_per_sm(int v, int kind)
     {
         int nb = 0;
-        cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<0>(), TXV<0> * TYV<0>, smem_v<0>())
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<1>(), TXV<1> * TYV<1>, smem_v<1>());
+        cudaError_t e = cudaErrorInvalidValue;
+        if (v == 1)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<1>(), TXV<1> * TYV<1>, smem_v<1>());
+        else if (kind & kStepAdvect) {
+            if constexpr (kAdv)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<0, true, true>(), TXV<0> * TYV<0>,
+                                                                  smem_v<0, true>());
+        } else if (kind)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<0, true>(), TXV<0> * TYV<0>, smem_v<0>());
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel<0>(), TXV<0> * TYV<0>, smem_v<0>());
         if (e != cudaSuccess) {
             cudaGetLastError();
             return 1;

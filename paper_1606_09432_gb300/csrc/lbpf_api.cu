@@ -44,7 +44,7 @@ struct lbpf_ctx {
     int n_items = 0, n_blocks = 0, items_cap = 0;
     int tile_v = 0, seg_len = 0, sms = 1;
     bool staged = false;  // step kernel with bulk-copy staging (staged_kernel.cuh)
-    int walls = 0;        // some domain has zero-flux walls: the step kernel's wall variant
+    int kind = 0;         // step kernel kind: kStepWalls (some domain has walls) | kStepAdvect
     // graphs of kGraphSteps steady-state launches, keyed by (cur, fcur, acur)
     cudaGraphExec_t graphs[8] = {};
     bool graphs_off = false;
@@ -133,7 +133,7 @@ static long long column_units(const lbpf_ctx* c, int v)
 
 static int blocks_per_sm(const lbpf_ctx* c, int v)
 {
-    return c->staged ? c->L->staged_blocks_per_sm() : c->L->blocks_per_sm(v);
+    return c->staged ? c->L->staged_blocks_per_sm() : c->L->blocks_per_sm(v, c->kind);
 }
 
 // Segment length balancing the per-item prologue (two extra planes) against
@@ -209,7 +209,7 @@ static std::string tune_key(const lbpf_ctx* c)
         h *= 1099511628211ULL;
     }
     snprintf(buf, sizeof(buf), "s2-lat%d-prec%d-grad%d-dom%d-%016llx-sm%d-k%d", c->lattice, c->precision, c->grad,
-             c->n_domains, h, c->sms, c->staged ? 1 : 0);
+             c->n_domains, h, c->sms, (c->staged ? 1 : 0) | (c->kind << 1));
     return buf;
 }
 
@@ -246,7 +246,7 @@ static double time_schedule(lbpf_ctx* c, int launches)
         if (cudaMemsetAsync(c->d_counters + c->cur, 0, sizeof(int), c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
         if ((c->staged ? c->L->step_staged(a, c->n_blocks, c->stream)
-                       : c->L->step(c->tile_v, c->walls, a, c->n_blocks, c->stream)) != cudaSuccess)
+                       : c->L->step(c->tile_v, c->kind, a, c->n_blocks, c->stream)) != cudaSuccess)
             break;
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
@@ -270,7 +270,7 @@ static int initial_schedule(lbpf_ctx* c)
         char k[200];
         int v, seg;
         while (fscanf(f, "%199s %d %d", k, &v, &seg) == 3)
-            if (key == k && v >= 0 && v < kNumTileVariants && seg >= 1) {
+            if (key == k && v >= 0 && v < (c->staged || c->kind ? 1 : kNumTileVariants) && seg >= 1) {
                 fclose(f);
                 c->tuned = "cache";
                 return set_schedule(c, v, seg);
@@ -294,7 +294,7 @@ static int autotune(lbpf_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     double best_t = 1e30, rule_t = 1e30;
     int best_v = 0, best_seg = default_segment(c, 0);
-    for (int v = 0; v < (c->staged || c->walls ? 1 : kNumTileVariants); ++v) {
+    for (int v = 0; v < (c->staged || c->kind ? 1 : kNumTileVariants); ++v) {
         const int L0 = default_segment(c, v);
         const int segs[3] = {L0, L0 / 2 > 8 ? L0 / 2 : 8, L0 * 2};
         for (int j = 0; j < 3; ++j) {
@@ -353,6 +353,17 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
             return fail(nullptr, LBPF_EINVAL, "domain %d: dx, dt, W0, tau0, kappa must be finite and > 0", k);
         if (!std::isfinite(d.lambda) || !std::isfinite(d.delta) || !std::isfinite(d.xi) || d.xi < 0)
             return fail(nullptr, LBPF_EINVAL, "domain %d: lambda, delta, xi must be finite (xi >= 0)", k);
+        if (!std::isfinite(d.adv[0]) || !std::isfinite(d.adv[1]) || !std::isfinite(d.adv[2]))
+            return fail(nullptr, LBPF_EINVAL, "domain %d: adv must be finite", k);
+        if (d.adv[0] != 0.0 || d.adv[1] != 0.0 || d.adv[2] != 0.0) {
+            if (precision != LBPF_FP64 && precision != LBPF_FP32)
+                return fail(nullptr, LBPF_EINVAL, "domain %d: an advective velocity needs full storage (FP64 or FP32)", k);
+            if (dim == 2 && d.adv[2] != 0.0)
+                return fail(nullptr, LBPF_EINVAL, "domain %d: adv[2] must be 0 on a 2D lattice", k);
+            if (((d.bc & LBPF_BC_WALL_X) && d.adv[0] != 0.0) || ((d.bc & LBPF_BC_WALL_Y) && d.adv[1] != 0.0) ||
+                ((d.bc & LBPF_BC_WALL_Z) && d.adv[2] != 0.0))
+                return fail(nullptr, LBPF_EINVAL, "domain %d: the velocity must be tangential to the walls", k);
+        }
         if (d.n_crystals < 1 || d.n_crystals > LBPF_MAX_CRYSTALS)
             return fail(nullptr, LBPF_EINVAL, "domain %d: n_crystals %d not in 1..%d", k, d.n_crystals, LBPF_MAX_CRYSTALS);
         for (int j = 0; j < d.n_crystals; ++j) {
@@ -401,7 +412,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         h.ny = d.ny;
         h.nz = d.nz;
         h.bc = d.bc;
-        if (d.bc) c->walls = 1;
+        if (d.bc) c->kind |= kStepWalls;
         h.n = (long long)d.nx * d.ny * d.nz;
         max_n = h.n > max_n ? h.n : max_n;
         // D_phi = (W0^2/tau0)(dt/dx^2), Eq. (LBE_RelaxationTime)
@@ -411,6 +422,10 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         // kappa = e^2 (eta_u - 1/2) dx^2 / dt, Eq. (ThermalDiffusivity)
         h.inv_eta_u = 1.0 / (d.kappa * d.dt / (e2u * d.dx * d.dx) + 0.5);
         h.xi_lu = d.xi * d.dx;
+        // advective heat equilibrium: a = v dt / (dx e^2)
+        h.advect = d.adv[0] != 0.0 || d.adv[1] != 0.0 || d.adv[2] != 0.0;
+        if (h.advect) c->kind |= kStepAdvect;
+        for (int a = 0; a < 3; ++a) h.adv[a] = d.adv[a] * d.dt / (d.dx * e2u);
         h.n_crystals = d.n_crystals;
         h.use_index = d.n_crystals > 1;
         for (int j = 0; j < d.n_crystals; ++j) {
@@ -426,6 +441,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
             if (rc == LBPF_OK) rc = dev_alloc(c, &h.phi[b], (size_t)h.n * c->rsize);
             if (rc == LBPF_OK) rc = dev_alloc(c, &h.aux[b], (size_t)h.n * c->rsize);
             if (rc == LBPF_OK && h.use_index) rc = dev_alloc(c, reinterpret_cast<void**>(&h.I[b]), (size_t)h.n);
+            if (rc == LBPF_OK && h.advect) rc = dev_alloc(c, &h.U[b], (size_t)h.n * c->rsize);
         }
         // zero state so that an unseeded domain holds finite values
         for (int b = 0; b < 2 && rc == LBPF_OK; ++b) {
@@ -433,7 +449,8 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
                 cudaMemsetAsync(h.f[b], 0, (size_t)c->Su * h.n * c->ssize, c->stream) != cudaSuccess ||
                 cudaMemsetAsync(h.phi[b], 0, (size_t)h.n * c->rsize, c->stream) != cudaSuccess ||
                 cudaMemsetAsync(h.aux[b], 0, (size_t)h.n * c->rsize, c->stream) != cudaSuccess ||
-                (h.use_index && cudaMemsetAsync(h.I[b], 0, (size_t)h.n, c->stream) != cudaSuccess))
+                (h.use_index && cudaMemsetAsync(h.I[b], 0, (size_t)h.n, c->stream) != cudaSuccess) ||
+                (h.advect && cudaMemsetAsync(h.U[b], 0, (size_t)h.n * c->rsize, c->stream) != cudaSuccess))
                 rc = fail(c, LBPF_ECUDA, "lbpf_create: cudaMemsetAsync failed");
         }
     }
@@ -444,7 +461,7 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         const char* kenv = getenv("LBPF_KERNEL");
         c->staged = L->step_staged != nullptr && kenv && strcmp(kenv, "staged") == 0;
         for (const DomainDev& h : c->dd)
-            if (h.nx % 8 != 0 || h.nx < 64 || h.use_index || h.bc) c->staged = false;
+            if (h.nx % 8 != 0 || h.nx < 64 || h.use_index || h.bc || h.advect) c->staged = false;
         if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
             c->sms = 1;
         for (int v = 0; v < kNumTileVariants && rc == LBPF_OK; ++v) {
@@ -592,7 +609,7 @@ static int launch_step(lbpf_ctx* c)
     if (c->staged)
         CK(c->L->step_staged(a, c->n_blocks, c->stream));
     else
-        CK(c->L->step(c->tile_v, c->walls, a, c->n_blocks, c->stream));
+        CK(c->L->step(c->tile_v, c->kind, a, c->n_blocks, c->stream));
     c->cur ^= 1;
     c->acur ^= 1;
     if (c->lagged) c->fcur ^= 1;
@@ -820,8 +837,9 @@ extern "C" int lbpf_set_schedule(lbpf_ctx* c, int tile_rows, int segment)
     for (int k = 0; k < kNumTileVariants; ++k)
         if (kTileRows[k] == tile_rows) v = k;
     if (v < 0 || segment < 1) return fail(c, LBPF_EINVAL, "lbpf_set_schedule: tile_rows must be 8 or 16, segment >= 1");
-    if ((c->staged || c->walls) && v != 0)
-        return fail(c, LBPF_EINVAL, "lbpf_set_schedule: 16-row tiles exist only for periodic domains (generic kernel)");
+    if ((c->staged || c->kind) && v != 0)
+        return fail(c, LBPF_EINVAL,
+                    "lbpf_set_schedule: 16-row tiles exist only for periodic domains without advection (generic kernel)");
     CK(cudaStreamSynchronize(c->stream));
     c->tune_pending = false;
     c->tuned = "set";

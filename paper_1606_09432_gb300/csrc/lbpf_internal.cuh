@@ -213,6 +213,13 @@ struct DomainDev {
     void* phi[2];       // phi field, arithmetic type
     void* aux[2];       // heat auxiliary field (see the step kernel)
     int8_t* I[2];       // crystal index field (use_index only)
+    // Advective heat equilibrium (advect only, full storage):
+    //   f_i^(0) = w_i u (1 + e_i . a),  a = v dt / (dx e^2)
+    // (physical axes; v the domain's uniform velocity), and U = u / eta_u of
+    // the aux time level, which the heat pull reads at the source node.
+    int advect;
+    double adv[3];
+    void* U[2];
 };
 
 // One thread block's work: a column of TX x TY sites over planes [z0, z1).
@@ -408,17 +415,21 @@ __device__ __forceinline__ void anisotropy(const CrystalDev& c, R Gx, R Gy, R Gz
 // ---------------------------------------------------------------------------
 // Launchers exported by the per-lattice translation units.
 // ---------------------------------------------------------------------------
+constexpr int kStepWalls = 1, kStepAdvect = 2;
+
 struct Launchers {
-    // Fused step over all work items, tile variant v (rows kTileRows[v]);
-    // walls != 0 selects the variant that handles zero-flux walls (built for
-    // variant 0 only).
-    cudaError_t (*step)(int v, int walls, const StepArgs& a, int n_blocks, cudaStream_t s);
+    // Fused step over all work items, tile variant v (rows kTileRows[v]).
+    // kind: 0 periodic domains only; kStepWalls: some domain has zero-flux
+    // walls; kStepAdvect: some domain has an advective heat equilibrium (full
+    // storage only; the kernel also handles walls).  Kinds other than 0 are
+    // built for variant 0 only.
+    cudaError_t (*step)(int v, int kind, const StepArgs& a, int n_blocks, cudaStream_t s);
     // Dynamic shared memory of variant v.
     size_t (*step_smem)(int v);
-    // Opt variant v (both wall variants) into its dynamic shared memory.
+    // Opt variant v (every kind built for it) into its dynamic shared memory.
     cudaError_t (*prepare)(int v);
-    // Resident blocks per SM of variant v.
-    int (*blocks_per_sm)(int v);
+    // Resident blocks per SM of variant v and step kind.
+    int (*blocks_per_sm)(int v, int kind);
     // Staged step kernel (staged_kernel.cuh; tile 32 x 8 of variant 0), or
     // nullptr where it is not built (2D, full storage, D3Q27).
     cudaError_t (*step_staged)(const StepArgs& a, int n_blocks, cudaStream_t s);

@@ -99,16 +99,30 @@ template <> struct CoefIO<double> {
     }
 };
 
+// Shared memory of the staged heat populations (2D, FP32 full storage) and
+// of the U ring (ADV), each rounded up to 16 bytes.
+template <class UL, class S, bool XZV>
+constexpr size_t stf_bytes(int RP)
+{
+    return (XZV && sizeof(typename S::T) == 4 && !S::dev) ? (((size_t)UL::Q * RP * sizeof(typename S::T) + 15) & ~size_t(15))
+                                                         : 0;
+}
+
 // One work item: the column (x0, y0) of one domain over planes [z0, z1).
 // WALLS: the domain may have zero-flux walls (mirror planes through the
 // boundary nodes, lbpf.h LBPF_BC_WALL_X): stencil indices beyond a wall are
 // reflected, and at a wall node every population whose source lies beyond
 // the wall takes the value of its mirrored partner (the bounce-back of Sec.
 // 3.3), for the phase-field and the heat populations alike.
-template <class PL, class UL, class S, int TXT, int TY, bool WALLS>
+// ADV (full storage): domains with a uniform velocity v use the advective
+// heat equilibrium f_j^(0) = w_j u (1 + e_j . a), a = v dt / (dx e^2), so
+// the heat pull gains w_j (e_j . a) U(x - e_j), U = u^{n-1} / eta_u, read
+// from a ring of U planes staged like h; the launch stores U^n beside aux^n.
+template <class PL, class UL, class S, int TXT, int TY, bool WALLS, bool ADV>
 __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
     static_assert(PL::D == 3 && UL::D == 3, "the step kernel marches along z (2D lattices through XZ)");
+    static_assert(!(ADV && S::dev), "the advective heat equilibrium is built for full storage only");
     constexpr int NT = TXT * TY;
     using R = typename S::Real;
     using T = typename S::T;
@@ -142,6 +156,9 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     // In 3D the extra shared memory costs more L1 than the copies save.
     constexpr bool STF = XZV && sizeof(T) == 4 && !DEV;
     T* s_f = reinterpret_cast<T*>(s_I + ((NPH * RP + 15) & ~15));
+    R* s_U = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(s_f) + stf_bytes<UL, S, XZV>(RP));
+    static_assert(!ADV || (sizeof(R) * (NPH * RP + NH * RP + NC * NCO * CP) + ((NPH * RP + 15) & ~15)) % 16 == 0,
+                  "the U ring is a cp.async 16-byte destination");
 
     const DomainDev& dm = args.doms[it.dom];
     const int nx = dm.nx, ny = XZV ? 1 : dm.ny, nz = XZV ? dm.ny : dm.nz;
@@ -164,6 +181,16 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     R* __restrict__ auxn = static_cast<R*>(dm.aux[args.acur ^ 1]);
     const int8_t* __restrict__ Ic = dm.I[args.cur];
     int8_t* __restrict__ In = dm.I[args.cur ^ 1];
+    // advective heat equilibrium: U at the aux time level, a in the kernel's
+    // axes (a 2D domain's y axis is the kernel's z)
+    const bool advect = ADV && dm.advect != 0;
+    const bool need_U = advect && collide;
+    const R* __restrict__ Uc = ADV ? static_cast<const R*>(dm.U[args.acur]) : nullptr;
+    R* __restrict__ Un = ADV ? static_cast<R*>(dm.U[args.acur ^ 1]) : nullptr;
+    const R ax = ADV ? R(dm.adv[0]) : R(0);
+    const R ay = (ADV && !XZV) ? R(dm.adv[1]) : R(0);
+    const R az = ADV ? R(XZV ? dm.adv[1] : dm.adv[2]) : R(0);
+    (void)ay;
 
     constexpr bool SR = UsesSR<S>::value;
     const uint32_t seed = SR ? (uint32_t)args.counters[2 + args.cur] : 0u;
@@ -227,6 +254,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const long long zo = (long long)wrapz(zp) * nxy;
         R* dphi = s_phi + sphi(zp) * RP;
         R* dh = s_h + sh(zp) * RP;
+        R* dU = s_U + sh(zp) * RP;
         int8_t* dI = s_I + sphi(zp) * RP;
         const int rows = th + 2 * HL;
         constexpr int EPC = 16 / (int)sizeof(R), NCH = TXT / EPC;
@@ -248,6 +276,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     const int k = ly * RX + XO + c * EPC;
                     cp16(dphi + k, phic + s);
                     if (need_h) cp16(dh + k, auxc + s);
+                    if (need_U) cp16(dU + k, Uc + s);
                 } else {
                     const int u = t - nint, ly = u >> 2, q = u & 3;
                     const int lx = q < 2 ? XO - 2 + q : XO + TXT + (q - 2);
@@ -255,6 +284,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                     const int k = ly * RX + lx;
                     cp4(dphi + k, phic + s);
                     if (need_h) cp4(dh + k, auxc + s);
+                    if (need_U) cp4(dU + k, Uc + s);
                 }
             }
             if (use_index)
@@ -270,6 +300,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                 const long long s = zo + (long long)wrapy(y0 + ly - HL) * nx + wrapx(x0 + lx - XO);
                 cp4(dphi + k, phic + s);
                 if (need_h) cp4(dh + k, auxc + s);
+                if (need_U) cp4(dU + k, Uc + s);
                 if (use_index) dI[k] = Ic[s];
             }
         }
@@ -311,6 +342,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const long long zo = (long long)wrapz(zp) * nxy;
         R* dphi = s_phi + sphi(zp) * RP;
         R* dh = s_h + sh(zp) * RP;
+        R* dU = s_U + sh(zp) * RP;
         int8_t* dI = s_I + sphi(zp) * RP;
         const int rows = th + 2 * HL;
         for (int k = tid; k < RX * rows; k += NT) {
@@ -320,6 +352,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             const R ph = phic[s];
             dphi[k] = ph;
             if (need_h) dh[k] = auxc[s] + R(0.5) * ph;
+            if (need_U) dU[k] = Uc[s];
             if (use_index) dI[k] = Ic[s];
         }
     };
@@ -391,6 +424,12 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                         const R fr = (STF && staged) ? to_real(s_f[j * RP + (py - ey) * RX + (px - ex)])
                                                      : to_real(fc[(long long)j * n + src]);
                         fj = om_u * fr + R(UL::w(j)) * hs;
+                        if constexpr (ADV) {
+                            if (advect && (ex | ey | ez)) {
+                                const R ea = R(ex) * ax + R(ey) * ay + R(ez) * az;
+                                fj += R(UL::w(j)) * ea * s_U[sh(zp - ez) * RP + (py - ey) * RX + (px - ex)];
+                            }
+                        }
                     } else {
                         const R dj = (j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]);
                         fj = R(UL::w(j)) * hs + om_u * dj;
@@ -433,6 +472,9 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                 }
             }
             if (inner) auxn[s] = DEV ? (u - R(0.5) * ph) : (u * ieu - R(0.5) * ph);
+            if constexpr (ADV) {
+                if (inner && advect) Un[s] = u * ieu;
+            }
 
             // gradient of phi^n (Sec. 4.2)
             R Gx = 0, Gy = 0, Gz = 0;
@@ -624,7 +666,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
 // The launch uses counter[cur] and clears counter[cur ^ 1] for the next step
 // (launches on one stream run in order; cur alternates every step).
 // Launch bounds ask for 1024 resident threads per SM (64 registers a thread).
-template <class PL, class UL, class S, int TXT, int TY, bool WALLS>
+template <class PL, class UL, class S, int TXT, int TY, bool WALLS, bool ADV = false>
 __global__ void __launch_bounds__(TXT * TY, 1024 / (TXT * TY)) step_kernel(const StepArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -640,12 +682,12 @@ __global__ void __launch_bounds__(TXT * TY, 1024 / (TXT * TY)) step_kernel(const
         __syncthreads();
         const int k = s_next;
         if (k >= args.n_items) break;
-        step_item<PL, UL, S, TXT, TY, WALLS>(args, args.items[k], smem_raw);
+        step_item<PL, UL, S, TXT, TY, WALLS, ADV>(args, args.items[k], smem_raw);
         __syncthreads();
     }
 }
 
-template <class PL, class UL, class S, int TXT, int TY>
+template <class PL, class UL, class S, int TXT, int TY, bool ADV = false>
 constexpr size_t step_smem_bytes()
 {
     using R = typename S::Real;
@@ -653,9 +695,8 @@ constexpr size_t step_smem_bytes()
     constexpr int XO = (IsXZ<PL>::value || sizeof(R) >= 8) ? 2 : 4;
     constexpr int RP = (TXT + 2 * XO) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
     constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
-    using T = typename S::T;
-    constexpr size_t stf = IsXZ<PL>::value && sizeof(T) == 4 && !S::dev ? (size_t)UL::Q * RP * sizeof(T) : 0;
-    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) + stf;
+    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) +
+           stf_bytes<UL, S, IsXZ<PL>::value>(RP) + (ADV ? sizeof(R) * (size_t)NH * RP : 0);
 }
 
 }  // namespace lbpf

@@ -44,7 +44,8 @@ class lbpf_domain(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("W0", C.c_double), ("tau0", C.c_double),
                 ("kappa", C.c_double), ("lam", C.c_double), ("delta", C.c_double), ("xi", C.c_double),
-                ("n_crystals", C.c_int), ("crystals", lbpf_crystal * LBPF_MAX_CRYSTALS)]
+                ("n_crystals", C.c_int), ("crystals", lbpf_crystal * LBPF_MAX_CRYSTALS),
+                ("adv", C.c_double * 3)]
 
 
 class lbpf_seed_t(C.Structure):
@@ -122,15 +123,17 @@ def make_crystal(kind=LBPF_AS_CUBIC100, eps=0.0, gamma=0.0, q=4, phi0=0.0) -> lb
 
 
 def make_domain(nx, ny, nz=1, *, dx, dt, W0, tau0, kappa, lam=0.0, delta=0.0, xi=1e-7, crystals=None,
-                bc=0) -> lbpf_domain:
+                bc=0, adv=(0.0, 0.0, 0.0)) -> lbpf_domain:
     """lam <= 0 selects lambda* (the library applies Eq. (Kinetic-Coeff) with
-    beta = 0); bc: LBPF_BC_WALL_* bits (0: periodic)."""
+    beta = 0); bc: LBPF_BC_WALL_* bits (0: periodic); adv: uniform velocity
+    of the advective heat equilibrium (physical units, full storage only)."""
     d = lbpf_domain()
     d.nx, d.ny, d.nz = nx, ny, nz
     d.bc = bc
     d.dx, d.dt, d.W0, d.tau0, d.kappa = dx, dt, W0, tau0, kappa
     d.lam = 0.0 if lam is None else lam
     d.delta, d.xi = delta, xi
+    d.adv[0], d.adv[1], d.adv[2] = (float(v) for v in adv)
     cl = list(crystals) if crystals else [make_crystal()]
     d.n_crystals = len(cl)
     for k, c in enumerate(cl):

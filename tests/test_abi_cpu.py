@@ -48,6 +48,23 @@ def test_invalid_arguments_rejected_before_gpu(L):
         assert L.lbpf_last_error(None)
 
 
+def test_invalid_velocity_rejected_before_gpu(L):
+    """The advective heat equilibrium: full storage only, no z component on
+    a 2D lattice, tangential to walls, finite."""
+    def dom(nz=1, bc=0, adv=(0.1, 0.0, 0.0)):
+        return L.make_domain(8, 8, nz, dx=1, dt=0.1, W0=1, tau0=1, kappa=1, bc=bc, adv=adv)
+    cases = [(dom(), L.LBPF_D2Q9_D2Q5, L.LBPF_FP32_FP16DEV),
+             (dom(), L.LBPF_D2Q9_D2Q5, L.LBPF_FP32_BF16DEV),
+             (dom(adv=(0, 0, 0.1)), L.LBPF_D2Q9_D2Q5, L.LBPF_FP64),
+             (dom(bc=L.LBPF_BC_WALL_X), L.LBPF_D2Q9_D2Q5, L.LBPF_FP64),
+             (dom(nz=8, bc=L.LBPF_BC_WALL_Z, adv=(0.1, 0.0, 0.2)), L.LBPF_D3Q15_D3Q7, L.LBPF_FP32),
+             (dom(adv=(float("nan"), 0, 0)), L.LBPF_D2Q9_D2Q5, L.LBPF_FP64)]
+    for d, lat, prec in cases:
+        with pytest.raises(L.LbpfError) as e:
+            L.lbpf_create([d], lat, L.LBPF_GRAD_DD, prec)
+        assert e.value.code == L.LBPF_EINVAL
+
+
 def test_null_context_is_safe(L):
     lib = L.load()
     assert lib.lbpf_destroy(None) == 0
