@@ -451,26 +451,22 @@ __device__ __forceinline__ void staged_item(const StepArgs& args, const WorkItem
                 const int nsl = ez != 0 ? 3 : 2;
                 const int f0 = G::first_slot(i, GNZ, G::GSL);
                 const R d = to_real(s_g[f0 + ring(z, nsl) * G::GSL + gt]);
-                d0 -= d;
-                gl = R(PL::w(i)) * phy + d;
+                d0 = sub_rn(d0, d);
+                gl = fma_rn(R(PL::w(i)), phy, d);
                 gp = to_real(s_g[f0 + ring(z - ez, nsl) * G::GSL + gt - ey * GX - ex]);
             } else {
-                gl = R(PL::w(0)) * phy + d0;
+                gl = fma_rn(R(PL::w(0)), phy, d0);
                 gp = d0;
             }
-            R ev = R(0);
-            if (ex) ev += R(ex) * vx;
-            if (ey) ev += R(ey) * vy;
-            if (ez) ev += R(ez) * vz;
-            const R v = c1 * gp - c2 * gl + R(PL::w(i)) * (cs + ev);
+            const R v = pull_new<R>(ex, ey, ez, R(PL::w(i)), c1, c2, cs, vx, vy, vz, gp, gl);
             gnew[i] = v;
-            phinew += v;
+            phinew = add_rn(phinew, v);
         }
         phin[s] = phinew;
         const uint32_t h = SR ? sr_hash((uint32_t)s, seed) : 0u;
 #pragma unroll
         for (int i = 1; i < QG; ++i)
-            store_dev(&gn[(long long)(i - 1) * n + s], gnew[i] - R(PL::w(i)) * phinew, h, (uint32_t)i);
+            store_dev(&gn[(long long)(i - 1) * n + s], fma_rn(-R(PL::w(i)), phinew, gnew[i]), h, (uint32_t)i);
     };
 
     // ---- the march ---------------------------------------------------------

@@ -46,6 +46,32 @@
 
 namespace lbpf {
 
+// Explicitly rounded arithmetic (no contraction), so that the output phases of
+// the step kernel and of the staged kernel round the same operations in the
+// same order (their results are compared bit for bit).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// New phase-field population of direction e = (ex, ey, ez) at y (Eq.
+// LBE_Eq_Phase divided by a_s^2, pull form): c1 gp - c2 gl + w (s + e . v),
+// rounded as a = ((s +- vx) +- vy) +- vz (zero components skipped), then
+// fma(w, a, fma(c1, gp, -(c2 gl))).
+template <class R>
+__device__ __forceinline__ R pull_new(int ex, int ey, int ez, R w, R c1, R c2, R cs, R vx, R vy, R vz, R gp, R gl)
+{
+    R a = cs;
+    if (ex) a = ex > 0 ? add_rn(a, vx) : sub_rn(a, vx);
+    if (ey) a = ey > 0 ? add_rn(a, vy) : sub_rn(a, vy);
+    if (ez) a = ez > 0 ? add_rn(a, vz) : sub_rn(a, vz);
+    return fma_rn(w, a, fma_rn(c1, gp, -mul_rn(c2, gl)));
+}
+
 // Collision coefficients of one site, (c1, c2, s, vx, vy, vz), in one plane
 // slot of 6 * CP values.  FP32: an array of float4 (c1, c2, s, vx) followed by
 // an array of float2 (vy, vz), so that a direction reads one or two vectors;
@@ -142,6 +168,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     constexpr int NH = 4;                                   // h ring depth (z .. z+3)
     constexpr int NC = 3;                                   // coefficient ring depth
     constexpr int NCO = 6;                                  // c1, c2, s, vx, vy, vz
+    constexpr int COP = NCO * CP;                           // reals of one coefficient plane
     constexpr int QG = PL::Q, QU = UL::Q;
     constexpr bool DEV = S::dev;
     (void)RY;
@@ -150,14 +177,14 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
     R* s_phi = reinterpret_cast<R*>(smem_raw);
     R* s_h = s_phi + NPH * RP;
     R* s_co = s_h + NH * RP;
-    int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * NCO * CP);
+    int8_t* s_I = reinterpret_cast<int8_t*>(s_co + NC * COP);
     // 2D, FP32 full storage: the heat populations f^{n-1}_j(x - e_j) of the
     // next coefficient plane are staged too (copied during the output phase).
     // In 3D the extra shared memory costs more L1 than the copies save.
     constexpr bool STF = XZV && sizeof(T) == 4 && !DEV;
     T* s_f = reinterpret_cast<T*>(s_I + ((NPH * RP + 15) & ~15));
     R* s_U = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(s_f) + stf_bytes<UL, S, XZV>(RP));
-    static_assert(!ADV || (sizeof(R) * (NPH * RP + NH * RP + NC * NCO * CP) + ((NPH * RP + 15) & ~15)) % 16 == 0,
+    static_assert(!ADV || (sizeof(R) * (NPH * RP + NH * RP + NC * COP) + ((NPH * RP + 15) & ~15)) % 16 == 0,
                   "the U ring is a cp.async 16-byte destination");
 
     const DomainDev& dm = args.doms[it.dom];
@@ -384,7 +411,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const long long zo = (long long)zw * nxy;
         const int zm = wrapz(zp - 1), zq = wrapz(zp + 1);
         const long long ozm = (long long)(zm - zw) * nxy, ozp = (long long)(zq - zw) * nxy;
-        R* dco = s_co + sco(zp) * NCO * CP;
+        R* dco = s_co + sco(zp) * COP;
         const int rows = th + 2 * HC;
         for (int k = tid; k < CX * rows; k += NT) {
             const int ly = k / CX, lx = k - ly * CX;
@@ -542,8 +569,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             // c1 phi (x): c1 (w_i phi + d_i) + w_i s = c1 d_i + w_i (s + c1 phi),
             // and s + c1 phi = (phi + (dt/tau0) Q_phi) / a_s^2
             const R sc = DEV ? (ph + qphi * Qphi) * iA2 : (ph * ieta + qphi * Qphi) * iA2;
-            CoefIO<R>::store(dco, CP, ly * CX + lx, (R(1) - ieta) * iA2, iA2 - R(1), sc,
-                             vf * Nx, vf * Ny, vf * Nz);
+            CoefIO<R>::store(dco, CP, ly * CX + lx, (R(1) - ieta) * iA2, iA2 - R(1), sc, vf * Nx, vf * Ny, vf * Nz);
         }
     };
 
@@ -579,7 +605,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             const int i = DEV ? (k + 1) % QG : k;
             const int ex = PL::ex(i), ey = PL::ey(i), ez = PL::ez(i);
             R c1, c2, cs, vx, vy, vz;
-            CoefIO<R>::load(s_co + sco(z - ez) * NCO * CP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
+            CoefIO<R>::load(s_co + sco(z - ez) * COP, CP, (cy - ey) * CX + (cx - ex), ey != 0 || ez != 0, c1, c2,
                             cs, vx, vy, vz);
             // gl: g_i(y) (the non-local term); gp: full storage g_i(x),
             // deviation storage d_i(x) (w_i phi(x) is in cs)
@@ -589,20 +615,16 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                 gp = i == 0 ? gl : to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
             } else if (i > 0) {
                 const R d = to_real(gc[(long long)(i - 1) * n + s]);
-                d0 -= d;
-                gl = R(PL::w(i)) * phy + d;
+                d0 = sub_rn(d0, d);
+                gl = fma_rn(R(PL::w(i)), phy, d);
                 gp = to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
             } else {
-                gl = R(PL::w(0)) * phy + d0;
+                gl = fma_rn(R(PL::w(0)), phy, d0);
                 gp = d0;
             }
-            R ev = R(0);
-            if (ex) ev += R(ex) * vx;
-            if (ey) ev += R(ey) * vy;
-            if (D == 3 && ez) ev += R(ez) * vz;
-            const R v = c1 * gp - c2 * gl + R(PL::w(i)) * (cs + ev);
+            const R v = pull_new<R>(ex, ey, ez, R(PL::w(i)), c1, c2, cs, vx, vy, vz, gp, gl);
             gnew[i] = v;
-            phinew += v;
+            phinew = add_rn(phinew, v);
         }
         if constexpr (WALLS) {
             if (bcm && on_wall(gx, gy, z)) {
@@ -621,7 +643,7 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             const uint32_t h = SR ? sr_hash((uint32_t)s, seed) : 0u;
 #pragma unroll
             for (int i = 1; i < QG; ++i)
-                store_dev(&gn[(long long)(i - 1) * n + s], gnew[i] - R(PL::w(i)) * phinew, h, (uint32_t)i);
+                store_dev(&gn[(long long)(i - 1) * n + s], fma_rn(-R(PL::w(i)), phinew, gnew[i]), h, (uint32_t)i);
         }
     };
 
@@ -694,8 +716,9 @@ constexpr size_t step_smem_bytes()
     constexpr int HL = IsXZ<PL>::value ? 0 : 2, HC = IsXZ<PL>::value ? 0 : 1;
     constexpr int XO = (IsXZ<PL>::value || sizeof(R) >= 8) ? 2 : 4;
     constexpr int RP = (TXT + 2 * XO) * (TY + 2 * HL), CP = (TXT + 2) * (TY + 2 * HC);
-    constexpr int NPH = 5, NH = 4, NC = 3, NCO = 6;
-    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * NCO * CP) + (((size_t)NPH * RP + 15) & ~size_t(15)) +
+    constexpr int NPH = 5, NH = 4, NC = 3;
+    constexpr int COP = 6 * CP;
+    return sizeof(R) * (size_t)(NPH * RP + NH * RP + NC * COP) + (((size_t)NPH * RP + 15) & ~size_t(15)) +
            stf_bytes<UL, S, IsXZ<PL>::value>(RP) + (ADV ? sizeof(R) * (size_t)NH * RP : 0);
 }
 
