@@ -424,6 +424,24 @@ int lbpf_net_delta(const float* phi0, const float* u0, const float* phi1, const 
 int lbpf_net_range_check(const float* phi, long long sites, float lo, float hi, unsigned int* count,
                          void* stream);
 
+/* One periodic 3x3 convolution layer of the surrogate network, on the
+ * tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation in tensor
+ * memory):
+ *   y[n][h][w][co] = act(b[co] + sum_tap sum_ci wt[tap][co][ci] x[n][h'][w'][ci]),
+ *   tap = 3 (dy + 1) + (dx + 1), h' = (h + dy) mod H, w' = (w + dx) mod W,
+ * act = ReLU if relu != 0, else the identity.  x: FP32 (n, H, W, cin); y:
+ * FP32 (n, H, W, cout); wt: BF16 bit patterns [9][cout][cin]; bias: FP32
+ * [cout] or NULL.  x is rounded to BF16 (to nearest even) on the way in.
+ * All pointers are device memory owned by the caller; the call is
+ * asynchronous on `stream`.  cin and cout multiples of 16, cout <= 256,
+ * n, H, W >= 1: else LBPF_EINVAL; LBPF_ECUDA if the launch fails. */
+int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias, float* y, int n, int H, int W, int cin,
+                    int cout, int relu, void* stream);
+/* *word = the convolution kernels' device error word: 0, or non-zero when a
+ * block's bounded wait for its tensor-core work gave up (the block then
+ * stops; its outputs are not written).  Synchronises the device first. */
+int lbpf_nn_conv_error(int* word);
+
 /* Release every resource of the context (NULL is accepted).  Synchronises
  * the stream first. */
 int lbpf_destroy(lbpf_ctx* ctx);

@@ -1,7 +1,7 @@
 // Kernels of the learned surrogate: a 2D U-Net on periodic fields, NHWC
-// activations in FP32, 3x3 convolutions on the tensor cores with BF16
-// operands and FP32 accumulation (mma.sync m16n8k16), weight gradients and
-// the small layers on the CUDA cores in FP32.
+// activations in FP32, 3x3 convolutions on the 5th-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory), the small
+// layers on the CUDA cores in FP32.
 //
 // Layouts:
 //   activations  x[n][h][w][c]            (c fastest), FP32
@@ -18,164 +18,258 @@
 
 namespace lbpf_nn {
 
-constexpr int kTile = 8;           // 8 x 8 output pixels per block
-constexpr int kHalo = kTile + 2;   // input tile with a 1-pixel halo
-constexpr int kWarps = 4;          // 16 pixels per warp
-
 __device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+// ---- 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
+//
+// y[p][co] = act(sum_tap sum_ci x[p + tap][ci] w[tap][co][ci] + b[co]):
+// D (M = 128 pixels of the flattened (n, h, w) order) x (N = cout) with
+// K = 9 cin, one tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = 128, N = cout,
+// K = 16) per 16 input channels of one tap, the accumulator in tensor memory
+// (TMEM).  The K loop runs over stages (tap, block of KC input channels), two
+// stage buffers in shared memory: while the tensor core works on stage s - 1,
+// the 128 threads gather stage s — each thread one pixel row of A (the tap's
+// neighbour, periodic in h and w, FP32 -> BF16) and the weight pieces of B
+// (cp.async) — into the no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, rows of a core matrix 16 bytes apart, 8-row groups 128 bytes
+// apart (SBO), 8-channel K slices one matrix apart (LBO).  One thread issues
+// the MMAs of a stage and commits them to the stage buffer's mbarrier, which
+// the gatherers of stage s + 2 wait on before they overwrite the buffer.
+// The epilogue reads the accumulator rows with tcgen05.ld (warp w owns TMEM
+// lanes 32w .. 32w + 31 = pixels), adds the bias, applies the ReLU and
+// stores FP32.  Waits are bounded (2 s by %globaltimer); on expiry the block
+// sets the error word and stops (conv_error()).
+
+__device__ int g_conv_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (bytes, multiples of 16),
+// no swizzle, descriptor version 1 (bits 46-48 = 0b001)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void ldmatrix_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1)
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
-// y = act(conv3x3(x, w) + bias).  Block: 8 x 8 output pixels of one image,
-// all COUT output channels; warp k owns pixels 16k .. 16k + 15 (two rows of
-// the tile).  The input tile (10 x 10 x CIN) and all weights are staged in
-// shared memory as BF16; rows of 8 channels (16 bytes) feed ldmatrix.
-// Rows are padded by 8 BF16 to spread shared-memory banks.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(32 * kWarps) conv3x3_fwd_kernel(const float* __restrict__ x,
-                                                                  const __nv_bfloat16* __restrict__ w,
-                                                                  const float* __restrict__ bias, float* __restrict__ y,
-                                                                  int H, int W, int relu)
+__device__ __forceinline__ void umma_commit(uint64_t* mbar)
 {
-    constexpr int XS = CIN + 8;  // padded pixel row of the input tile
-    constexpr int WS = CIN + 8;  // padded cout row of a weight tap
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16* s_x = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-    __nv_bfloat16* s_w = s_x + kHalo * kHalo * XS;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
 
-    const int tiles_x = W / kTile;
-    const int tile = blockIdx.x;
-    const int img = blockIdx.y;
-    const int ty0 = (tile / tiles_x) * kTile, tx0 = (tile % tiles_x) * kTile;
-    const float* xi = x + (size_t)img * H * W * CIN;
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
-    for (int e = threadIdx.x; e < kHalo * kHalo * CIN; e += blockDim.x) {
-        const int c = e % CIN, p = e / CIN;
-        const int hy = p / kHalo, hx = p % kHalo;
-        const int gy = wrap_i(ty0 + hy - 1, H), gx = wrap_i(tx0 + hx - 1, W);
-        s_x[p * XS + c] = __float2bfloat16_rn(xi[((size_t)gy * W + gx) * CIN + c]);
+// Wait for the completion of phase `parity` of an mbarrier, at most ~2 s;
+// false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(mbar);
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "r"(1000000u)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
     }
-    for (int e = threadIdx.x; e < 9 * COUT * CIN; e += blockDim.x) {
-        const int ci = e % CIN, r = e / CIN;  // r = tap * COUT + co
-        s_w[r * WS + ci] = w[e];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+constexpr int kConvM = 128;  // pixels per block (one TMEM lane each)
+
+__global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restrict__ x,
+                                                            const __nv_bfloat16* __restrict__ w,
+                                                            const float* __restrict__ bias, float* __restrict__ y,
+                                                            long long P, int H, int W, int cin, int cout, int KC,
+                                                            int relu, uint32_t tmem_cols)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t a_bytes = (size_t)kConvM * KC * 2, b_bytes = (size_t)cout * KC * 2;
+    auto sA = [&](int b) { return smem_raw + b * a_bytes; };
+    auto sB = [&](int b) { return smem_raw + 2 * a_bytes + b * b_bytes; };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    // this thread's pixel row
+    const long long p = (long long)blockIdx.x * kConvM + tid;
+    const bool valid = p < P;
+    const long long HW = (long long)H * W;
+    const long long img = valid ? p / HW : 0;
+    const int rem = valid ? (int)(p - img * HW) : 0;
+    const int py = rem / W, px = rem - py * W;
+    const float* ximg = x + img * HW * cin;
 
-    // ldmatrix x4 for A (16 pixels x 16 channels): lanes 0-15 address the
-    // rows (pixels) for channels k0..k0+7, lanes 16-31 for k0+8..k0+15.
-    const int arow = lane & 15;
-    const int apix = warp * 16 + arow;  // pixel within the 8 x 8 tile
-    const int ay = apix / kTile, ax = apix % kTile;
-    const int acol = (lane >> 4) * 8;
-    // ldmatrix x2 for B (16 cin x 8 cout, stored cout-major): lanes 0-7 rows
-    // (cout) for cin k0..k0+7, lanes 8-15 for k0+8..k0+15.
-    const int brow = lane & 7;
-    const int bcol = ((lane >> 3) & 1) * 8;
-
+    const int nkb = cin / KC, S = 9 * nkb;
+    const uint32_t idesc = umma_idesc_bf16(kConvM, cout);
+    bool ok = true;
+    int issued = 0;  // stages committed
+    for (int s = 0; s < S && ok; ++s) {
+        const int buf = s & 1, tap = s / nkb, c0 = (s - tap * nkb) * KC;
+        if (s >= 2 && !mbar_wait_bounded(&s_mbar[buf], ((s - 2) >> 1) & 1)) {
+            atomicOr(&g_conv_error, 1);
+            ok = false;
+            break;
+        }
+        // A: row tid = x at the tap's neighbour, channels c0 .. c0 + KC
+        {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            int yy = py + dy, xx = px + dx;
+            yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            const float4* src = reinterpret_cast<const float4*>(ximg + ((long long)yy * W + xx) * cin + c0);
+            unsigned char* dst = sA(buf) + tid * 16;
+            for (int k8 = 0; k8 < KC / 8; ++k8) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (valid) {
+                    const float4 f0 = __ldg(src + 2 * k8), f1 = __ldg(src + 2 * k8 + 1);
+                    v = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                                   pack_bf16(f1.z, f1.w));
+                }
+                *reinterpret_cast<uint4*>(dst + (size_t)k8 * kConvM * 16) = v;
+            }
+        }
+        // B: 16-byte pieces w[tap][co][c0 + 8 k8 ..] -> [k8][co]
+        for (int e = tid; e < cout * (KC / 8); e += kConvM) {
+            const int co = e % cout, k8 = e / cout;
+            const __nv_bfloat16* g = w + ((size_t)tap * cout + co) * cin + c0 + 8 * k8;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             smem_u32(sB(buf) + (size_t)k8 * cout * 16 + co * 16)),
+                         "l"(g));
+        }
+        asm volatile("cp.async.commit_group;");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(sA(buf)), b0 = smem_u32(sB(buf));
+            for (int k16 = 0; k16 < KC / 16; ++k16) {
+                const uint64_t ad = umma_desc(a0 + k16 * 2 * kConvM * 16, kConvM * 16, 128);
+                const uint64_t bd = umma_desc(b0 + k16 * 2 * cout * 16, cout * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (s > 0 || k16 > 0) ? 1u : 0u);
+            }
+            umma_commit(&s_mbar[buf]);
+        }
+        issued = s + 1;
+    }
+    // the last committed stage covers every MMA issued before it
+    bool done = false;
+    if (issued > 0) {
+        const int last = issued - 1;
+        done = mbar_wait_bounded(&s_mbar[last & 1], (last >> 1) & 1);
+        if (!done) atomicOr(&g_conv_error, 2);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && done) {
+        float* out = y + p * cout;
+        for (int c = 0; c < cout; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (valid) {
+                float v[8];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const uint32_t a_base = (uint32_t)__cvta_generic_to_shared(s_x + ((ay + 1 + dy) * kHalo + (ax + 1 + dx)) * XS + acol);
-#pragma unroll
-        for (int k0 = 0; k0 < CIN; k0 += 16) {
-            uint32_t a0, a1, a2, a3;
-            ldmatrix_x4(a_base + k0 * 2, a0, a1, a2, a3);
-#pragma unroll
-            for (int n = 0; n < COUT / 8; ++n) {
-                uint32_t b0, b1;
-                const uint32_t b_addr =
-                    (uint32_t)__cvta_generic_to_shared(s_w + (tap * COUT + n * 8 + brow) * WS + k0 + bcol);
-                ldmatrix_x2(b_addr, b0, b1);
-                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = __uint_as_float(r[j]) + (bias ? bias[c + j] : 0.f);
+                    if (relu) v[j] = fmaxf(v[j], 0.f);
+                }
+                reinterpret_cast<float4*>(out + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<float4*>(out + c)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
     }
-
-    // C fragment: rows lane/4 and lane/4 + 8 (pixels), cols 2 (lane%4) + {0,1}
-    float* yi = y + (size_t)img * H * W * COUT;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int pix = warp * 16 + (lane >> 2) + half * 8;
-        const int gy = ty0 + pix / kTile, gx = tx0 + pix % kTile;
-        float* out = yi + ((size_t)gy * W + gx) * COUT;
-#pragma unroll
-        for (int n = 0; n < COUT / 8; ++n) {
-            const int co = n * 8 + (lane & 3) * 2;
-            float v0 = acc[n][half * 2 + 0], v1 = acc[n][half * 2 + 1];
-            if (bias) {
-                v0 += bias[co];
-                v1 += bias[co + 1];
-            }
-            if (relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            *reinterpret_cast<float2*>(out + co) = make_float2(v0, v1);
-        }
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
-template <int CIN, int COUT>
-static cudaError_t conv_launch(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int N, int H, int W,
-                               int relu, cudaStream_t s)
+// Input channels a stage: all of them up to 64, else the largest of 64, 48,
+// 32, 16 dividing cin.
+static int conv_kc(int cin)
 {
-    const size_t smem = sizeof(__nv_bfloat16) * ((size_t)kHalo * kHalo * (CIN + 8) + 9 * COUT * (CIN + 8));
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3x3_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid((W / kTile) * (H / kTile), N);
-    conv3x3_fwd_kernel<CIN, COUT><<<grid, 32 * kWarps, smem, s>>>(x, w, bias, y, H, W, relu);
-    return cudaGetLastError();
+    if (cin <= 64) return cin;
+    for (int kc : {64, 48, 32, 16})
+        if (cin % kc == 0) return kc;
+    return 16;
 }
 
 cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int N, int H, int W,
                         int cin, int cout, int relu, cudaStream_t s)
 {
-    if (H % kTile || W % kTile) return cudaErrorInvalidValue;
-#define LBPF_NN_CASE(CI, CO) \
-    if (cin == CI && cout == CO) return conv_launch<CI, CO>(x, w, bias, y, N, H, W, relu, s);
-    LBPF_NN_CASE(16, 16)
-    LBPF_NN_CASE(16, 32)
-    LBPF_NN_CASE(32, 16)
-    LBPF_NN_CASE(32, 32)
-    LBPF_NN_CASE(32, 64)
-    LBPF_NN_CASE(64, 32)
-    LBPF_NN_CASE(64, 64)
-    LBPF_NN_CASE(48, 16)
-    LBPF_NN_CASE(16, 48)
-    LBPF_NN_CASE(96, 32)
-    LBPF_NN_CASE(32, 96)
-#undef LBPF_NN_CASE
-    return cudaErrorInvalidValue;
+    if (cin % 16 || cout % 16 || cin < 16 || cout < 16 || cout > 256 || H < 1 || W < 1) return cudaErrorInvalidValue;
+    const int KC = conv_kc(cin);
+    const size_t smem = 2 * ((size_t)kConvM * KC * 2 + (size_t)cout * KC * 2);
+    static int attr_bytes = 0;
+    if ((int)smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = (int)smem;
+    }
+    uint32_t cols = 32;
+    while ((int)cols < cout) cols <<= 1;
+    const long long P = (long long)N * H * W;
+    const long long blocks = (P + kConvM - 1) / kConvM;
+    conv3x3_tc_kernel<<<(unsigned)blocks, kConvM, smem, s>>>(x, w, bias, y, P, H, W, cin, cout, KC, relu, cols);
+    return cudaGetLastError();
+}
+
+int conv_error()
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_conv_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return v;
 }
 
 // Weights for the data gradient: dX = conv3x3(dY, wt) with

@@ -6,10 +6,13 @@
 
 namespace lbpf_nn {
 
-// y = act(conv3x3(x, w) + bias), periodic padding; H, W multiples of 8;
-// (cin, cout) one of the instantiated pairs.  w: BF16 [tap][cout][cin].
+// y = act(conv3x3(x, w) + bias), periodic padding, on the tensor cores
+// (tcgen05); cin, cout multiples of 16, cout <= 256.  w: BF16 [tap][cout][cin].
 cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int N, int H, int W,
                         int cin, int cout, int relu, cudaStream_t s);
+// Error word of the convolution kernels (1, 2: a bounded wait of a block
+// gave up; -1: unreadable); 0 when every wait completed.
+int conv_error();
 // wt[tap][ci][co] = w[8 - tap][co][ci]: weights of the data-gradient convolution.
 cudaError_t flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wt, int cin, int cout, cudaStream_t s);
 // dw[tap][co][ci] += sum_p dy[p][co] x[p + tap][ci]

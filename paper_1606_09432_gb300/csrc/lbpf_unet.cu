@@ -346,6 +346,7 @@ extern "C" int lbpf_net_train_step(lbpf_net* net, const float* x, const float* t
     if (loss) {
         NK(cudaMemcpyAsync(loss, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, net->stream));
         NK(cudaStreamSynchronize(net->stream));
+        if (conv_error() != 0) return net_fail(net, LBPF_ETIMEOUT, "a convolution block's bounded wait gave up");
     }
     return LBPF_OK;
 }
@@ -379,4 +380,26 @@ extern "C" int lbpf_net_range_check(const float* phi, long long sites, float lo,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(count, 0, sizeof(unsigned int), s) != cudaSuccess) return LBPF_ECUDA;
     return range_count(phi, sites, lo, hi, count, s) == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
+}
+
+extern "C" int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias, float* y, int n, int H, int W,
+                               int cin, int cout, int relu, void* stream)
+{
+    if (!x || !wt || !y || n < 1 || H < 1 || W < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 || cout > 256)
+        return LBPF_EINVAL;
+    return conv3x3_fwd(x, static_cast<const __nv_bfloat16*>(wt), bias, y, n, H, W, cin, cout, relu,
+                       static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? LBPF_OK
+               : LBPF_ECUDA;
+}
+
+extern "C" int lbpf_nn_conv_error(int* word)
+{
+    if (!word) return LBPF_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return LBPF_ECUDA;
+    }
+    *word = conv_error();
+    return *word < 0 ? LBPF_ECUDA : LBPF_OK;
 }

@@ -33,7 +33,7 @@ EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_
             "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
             "lbpf_net_get_params", "lbpf_net_set_params", "lbpf_net_forward", "lbpf_net_backward",
             "lbpf_net_train_step", "lbpf_net_assemble", "lbpf_net_apply", "lbpf_net_delta",
-            "lbpf_net_range_check", "lbpf_net_set_loss_weight"]
+            "lbpf_net_range_check", "lbpf_net_set_loss_weight", "lbpf_nn_conv3x3", "lbpf_nn_conv_error"]
 
 
 class lbpf_crystal(C.Structure):
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.lbpf_net_apply.argtypes = [vp, vp, vp, C.c_longlong, vp]
     lib.lbpf_net_delta.argtypes = [vp, vp, vp, vp, vp, C.c_longlong, vp]
     lib.lbpf_net_range_check.argtypes = [vp, C.c_longlong, C.c_float, C.c_float, vp, vp]
+    lib.lbpf_nn_conv3x3.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    lib.lbpf_nn_conv_error.argtypes = [C.POINTER(C.c_int)]
     for name in EXPORTED:
         lib[name].restype = C.c_int
     lib.lbpf_last_error.restype = C.c_char_p
@@ -431,3 +433,24 @@ def net_range_check(phi, lo, hi, count, stream=None):
                                      C.c_void_p(stream) if stream else None)
     if rc != LBPF_OK:
         raise LbpfError(rc, "lbpf_net_range_check failed")
+
+
+def nn_conv3x3(x, wt, bias, y, relu=False, stream=None):
+    """One periodic 3x3 convolution on the tensor cores: x (n, H, W, cin) and
+    y (n, H, W, cout) float32 CUDA tensors, wt a (9, cout, cin) bfloat16 (or
+    int16 bit-pattern) CUDA tensor, bias a (cout,) float32 CUDA tensor or None."""
+    n, H, W, cin = x.shape
+    cout = y.shape[-1]
+    rc = load().lbpf_nn_conv3x3(_dptr(x), _dptr(wt), _dptr(bias) if bias is not None else None, _dptr(y), n, H, W,
+                                cin, cout, int(bool(relu)), C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_nn_conv3x3 failed")
+
+
+def nn_conv_error():
+    """The convolution kernels' device error word (synchronises the device)."""
+    w = C.c_int(0)
+    rc = load().lbpf_nn_conv_error(C.byref(w))
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_nn_conv_error failed")
+    return w.value
