@@ -437,6 +437,15 @@ int lbpf_net_range_check(const float* phi, long long sites, float lo, float hi, 
  * n, H, W >= 1: else LBPF_EINVAL; LBPF_ECUDA if the launch fails. */
 int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias, float* y, int n, int H, int W, int cin,
                     int cout, int relu, void* stream);
+/* Weight gradient of that layer, added to dwt:
+ *   dwt[tap][co][ci] += sum_n,h,w dy[n][h][w][co] x[n][h'][w'][ci]
+ * (h', w' as above), on the tensor cores with x and dy rounded to BF16 (to
+ * nearest even) and FP32 accumulation; dwt FP32 [9][cout][cin].  Device
+ * pointers, asynchronous on `stream`; the sum's order varies from call to
+ * call (FP32 atomics).  cin, cout multiples of 16 (cin above 256 a multiple
+ * of 32), n, H, W >= 1: else LBPF_EINVAL; LBPF_ECUDA if the launch fails. */
+int lbpf_nn_conv3x3_wgrad(const float* x, const float* dy, float* dwt, int n, int H, int W, int cin, int cout,
+                          void* stream);
 /* *word = the convolution kernels' device error word: 0, or non-zero when a
  * block's bounded wait for its tensor-core work gave up (the block then
  * stops; its outputs are not written).  Synchronises the device first. */

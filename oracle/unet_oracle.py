@@ -81,8 +81,11 @@ def conv3x3_dgrad(dy, w, emulate=False):
     return dx
 
 
-def conv3x3_wgrad(x, dy):
-    """dw[tap][co][ci] = sum_p dy[p][co] x[p + tap][ci] (FP64)."""
+def conv3x3_wgrad(x, dy, emulate=False):
+    """dw[tap][co][ci] = sum_p dy[p][co] x[p + tap][ci] (FP64; with emulate
+    both operands rounded to BF16 first, as the tensor-core kernel does)."""
+    if emulate:
+        x, dy = bf16(x), bf16(dy)
     co, ci = dy.shape[-1], x.shape[-1]
     dw = np.zeros((9, co, ci))
     for tap in range(9):
@@ -147,7 +150,7 @@ def backward(p, c, dout, emulate=False):
 
     def cvb(k, a_in, y, dy, need_dx=True):
         dy = dy * (y > 0)
-        grads[k] = (conv3x3_wgrad(a_in, dy), dy.sum(axis=(0, 1, 2)))
+        grads[k] = (conv3x3_wgrad(a_in, dy, emulate), dy.sum(axis=(0, 1, 2)))
         return conv3x3_dgrad(dy, L[k][0], emulate) if need_dx else None
 
     ghw = np.einsum("nhwo,nhwi->oi", dout, c["d1"])

@@ -18,8 +18,6 @@
 
 namespace lbpf_nn {
 
-__device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
 // ---- 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
 //
 // y[p][co] = act(sum_tap sum_ci x[p + tap][ci] w[tap][co][ci] + b[co]):
@@ -290,41 +288,172 @@ cudaError_t flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wt, int cin, int
     return cudaGetLastError();
 }
 
-// dw[tap][co][ci] += sum over pixels p of dy[p][co] * x[p + tap][ci] (FP32).
-// Block: one image row band of `rows` rows; thread t accumulates entries
-// (tap, co, ci) = t, t + blockDim, ... over the band's pixels and adds them to
-// dw atomically.
-__global__ void conv3x3_wgrad_kernel(const float* __restrict__ x, const float* __restrict__ dy, float* dw, int N, int H,
-                                     int W, int cin, int cout, int rows)
+// ---- weight gradient on the tensor cores
+//
+// dw[tap][co][ci] += sum_p dy[p][co] x[p + tap][ci]: per block one tap, one
+// tile of 128 output channels (M; rows beyond cout are zero) and one tile of
+// nci input channels (N), over a range of pixels (K) in stages of 64:
+// A[co][p] = dy (BF16), B[ci][p] = x at the tap's neighbour (BF16), both
+// gathered transposed into the no-swizzle K-major layout (8 pixels of one
+// channel per 16-byte row of a core matrix).  Double-buffered stages,
+// mbarrier completion and bounded waits as in conv3x3_tc_kernel; the block's
+// partial sums leave tensor memory through tcgen05.ld and are added to dw
+// with FP32 atomics.
+constexpr int kWgK = 64;  // pixels a stage
+
+__global__ void __launch_bounds__(kConvM) conv3x3_wgrad_tc_kernel(const float* __restrict__ x,
+                                                                  const float* __restrict__ dy, float* dw, long long P,
+                                                                  int H, int W, int cin, int cout, int nci,
+                                                                  long long KP, uint32_t tmem_cols)
 {
-    const int bands = (H + rows - 1) / rows;
-    const int img = blockIdx.x / bands, y0 = (blockIdx.x % bands) * rows;
-    const int y1 = min(H, y0 + rows);
-    const float* xi = x + (size_t)img * H * W * cin;
-    const float* di = dy + (size_t)img * H * W * cout;
-    const int entries = 9 * cout * cin;
-    for (int e = threadIdx.x; e < entries; e += blockDim.x) {
-        const int ci = e % cin, r = e / cin;
-        const int co = r % cout, tap = r / cout;
-        const int ddy = tap / 3 - 1, ddx = tap % 3 - 1;
-        float acc = 0.f;
-        for (int yy = y0; yy < y1; ++yy) {
-            const int sy = wrap_i(yy + ddy, H);
-            for (int xx = 0; xx < W; ++xx) {
-                const int sx = wrap_i(xx + ddx, W);
-                acc += di[((size_t)yy * W + xx) * cout + co] * xi[((size_t)sy * W + sx) * cin + ci];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ long long s_q[2][kWgK];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tap = blockIdx.z;
+    const int n_ntiles = cin / nci;
+    const int co0 = (blockIdx.y / n_ntiles) * kConvM, ci0 = (blockIdx.y % n_ntiles) * nci;
+    const long long p0 = (long long)blockIdx.x * KP, p1 = p0 + KP < P ? p0 + KP : P;
+    const size_t a_bytes = (size_t)kConvM * kWgK * 2, b_bytes = (size_t)nci * kWgK * 2;
+    auto sA = [&](int b) { return smem_raw + b * a_bytes; };
+    auto sB = [&](int b) { return smem_raw + 2 * a_bytes + b * b_bytes; };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+
+    const int dyy = tap / 3 - 1, dxx = tap % 3 - 1;
+    const long long HW = (long long)H * W;
+    const int co = co0 + tid;  // this thread's A row
+    const uint32_t idesc = umma_idesc_bf16(kConvM, nci);
+    const int S = (int)((p1 - p0 + kWgK - 1) / kWgK);
+    bool ok = true;
+    int issued = 0;
+    for (int s = 0; s < S && ok; ++s) {
+        const int buf = s & 1;
+        const long long pb = p0 + (long long)s * kWgK;
+        if (s >= 2 && !mbar_wait_bounded(&s_mbar[buf], ((s - 2) >> 1) & 1)) {
+            atomicOr(&g_conv_error, 4);
+            ok = false;
+            break;
+        }
+        if (tid < kWgK) {  // the stage's pixels and their neighbours at the tap
+            const long long pp = pb + tid;
+            long long q = -1;
+            if (pp < p1) {
+                const long long img = pp / HW;
+                const int rem = (int)(pp - img * HW), py = rem / W, px = rem - py * W;
+                int yy = py + dyy, xx = px + dxx;
+                yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+                xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+                q = img * HW + (long long)yy * W + xx;
+            }
+            s_q[buf][tid] = q;
+        }
+        __syncthreads();
+        // A: row co, pixels pb .. pb + 63 of dy
+        for (int k8 = 0; k8 < kWgK / 8; ++k8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const long long pp = pb + 8 * k8 + j;
+                v[j] = (co < cout && pp < p1) ? __ldg(dy + pp * cout + co) : 0.f;
+            }
+            *reinterpret_cast<uint4*>(sA(buf) + (size_t)k8 * kConvM * 16 + tid * 16) =
+                make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+        }
+        // B: row ci, the same pixels' neighbours in x
+        for (int n = tid; n < nci; n += kConvM) {
+            const int ci = ci0 + n;
+            for (int k8 = 0; k8 < kWgK / 8; ++k8) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long q = s_q[buf][8 * k8 + j];
+                    v[j] = q >= 0 ? __ldg(x + q * cin + ci) : 0.f;
+                }
+                *reinterpret_cast<uint4*>(sB(buf) + (size_t)k8 * nci * 16 + n * 16) = make_uint4(
+                    pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
             }
         }
-        atomicAdd(&dw[e], acc);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(sA(buf)), b0 = smem_u32(sB(buf));
+            for (int k16 = 0; k16 < kWgK / 16; ++k16) {
+                const uint64_t ad = umma_desc(a0 + k16 * 2 * kConvM * 16, kConvM * 16, 128);
+                const uint64_t bd = umma_desc(b0 + k16 * 2 * nci * 16, nci * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (s > 0 || k16 > 0) ? 1u : 0u);
+            }
+            umma_commit(&s_mbar[buf]);
+        }
+        issued = s + 1;
     }
+    bool done = false;
+    if (issued > 0) {
+        const int last = issued - 1;
+        done = mbar_wait_bounded(&s_mbar[last & 1], (last >> 1) & 1);
+        if (!done) atomicOr(&g_conv_error, 8);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && done) {
+        for (int c = 0; c < nci; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (co < cout) {
+                float* d = dw + ((size_t)tap * cout + co) * cin + ci0 + c;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) atomicAdd(d + j, __uint_as_float(r[j]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 cudaError_t conv3x3_wgrad(const float* x, const float* dy, float* dw, int N, int H, int W, int cin, int cout,
                           cudaStream_t s)
 {
-    const int rows = 4;
-    const int blocks = N * ((H + rows - 1) / rows);
-    conv3x3_wgrad_kernel<<<blocks, 256, 0, s>>>(x, dy, dw, N, H, W, cin, cout, rows);
+    const int n_ntiles = (cin + 255) / 256;
+    if (cin % 16 || cout % 16 || cin < 16 || cout < 16 || cin % (16 * n_ntiles)) return cudaErrorInvalidValue;
+    const int nci = cin / n_ntiles, n_mtiles = (cout + kConvM - 1) / kConvM;
+    const long long P = (long long)N * H * W;
+    // about four blocks an SM in all: pixel chunks of a multiple of 64
+    long long chunks = (4LL * 152 + 9 * n_mtiles * n_ntiles - 1) / (9 * n_mtiles * n_ntiles);
+    long long KP = (P + chunks - 1) / chunks;
+    KP = ((KP + kWgK - 1) / kWgK) * kWgK;
+    chunks = (P + KP - 1) / KP;
+    const size_t smem = 2 * ((size_t)kConvM * kWgK * 2 + (size_t)nci * kWgK * 2);
+    static int attr_bytes = 0;
+    if ((int)smem > attr_bytes) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = (int)smem;
+    }
+    uint32_t cols = 32;
+    while ((int)cols < nci) cols <<= 1;
+    dim3 grid((unsigned)chunks, (unsigned)(n_mtiles * n_ntiles), 9);
+    conv3x3_wgrad_tc_kernel<<<grid, kConvM, smem, s>>>(x, dy, dw, P, H, W, cin, cout, nci, KP, cols);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,8 @@ cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bia
 int conv_error();
 // wt[tap][ci][co] = w[8 - tap][co][ci]: weights of the data-gradient convolution.
 cudaError_t flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wt, int cin, int cout, cudaStream_t s);
-// dw[tap][co][ci] += sum_p dy[p][co] x[p + tap][ci]
+// dw[tap][co][ci] += sum_p dy[p][co] x[p + tap][ci], BF16 operands on the tensor
+// cores, FP32 accumulation; cin, cout multiples of 16 (cin > 256: of 32).
 cudaError_t conv3x3_wgrad(const float* x, const float* dy, float* dw, int N, int H, int W, int cin, int cout,
                           cudaStream_t s);
 cudaError_t bias_grad(const float* dy, float* db, long long P, int c, cudaStream_t s);

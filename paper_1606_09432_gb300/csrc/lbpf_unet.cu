@@ -393,6 +393,17 @@ extern "C" int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias
                : LBPF_ECUDA;
 }
 
+extern "C" int lbpf_nn_conv3x3_wgrad(const float* x, const float* dy, float* dwt, int n, int H, int W, int cin,
+                                     int cout, void* stream)
+{
+    if (!x || !dy || !dwt || n < 1 || H < 1 || W < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 ||
+        (cin > 256 && cin % 32))
+        return LBPF_EINVAL;
+    return conv3x3_wgrad(x, dy, dwt, n, H, W, cin, cout, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? LBPF_OK
+               : LBPF_ECUDA;
+}
+
 extern "C" int lbpf_nn_conv_error(int* word)
 {
     if (!word) return LBPF_EINVAL;

@@ -33,7 +33,8 @@ EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_
             "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
             "lbpf_net_get_params", "lbpf_net_set_params", "lbpf_net_forward", "lbpf_net_backward",
             "lbpf_net_train_step", "lbpf_net_assemble", "lbpf_net_apply", "lbpf_net_delta",
-            "lbpf_net_range_check", "lbpf_net_set_loss_weight", "lbpf_nn_conv3x3", "lbpf_nn_conv_error"]
+            "lbpf_net_range_check", "lbpf_net_set_loss_weight", "lbpf_nn_conv3x3", "lbpf_nn_conv3x3_wgrad",
+            "lbpf_nn_conv_error"]
 
 
 class lbpf_crystal(C.Structure):
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.lbpf_net_delta.argtypes = [vp, vp, vp, vp, vp, C.c_longlong, vp]
     lib.lbpf_net_range_check.argtypes = [vp, C.c_longlong, C.c_float, C.c_float, vp, vp]
     lib.lbpf_nn_conv3x3.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    lib.lbpf_nn_conv3x3_wgrad.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     lib.lbpf_nn_conv_error.argtypes = [C.POINTER(C.c_int)]
     for name in EXPORTED:
         lib[name].restype = C.c_int
@@ -445,6 +447,17 @@ def nn_conv3x3(x, wt, bias, y, relu=False, stream=None):
                                 cin, cout, int(bool(relu)), C.c_void_p(stream) if stream else None)
     if rc != LBPF_OK:
         raise LbpfError(rc, "lbpf_nn_conv3x3 failed")
+
+
+def nn_conv3x3_wgrad(x, dy, dwt, stream=None):
+    """dwt (9, cout, cin) float32 += the weight gradient of one 3x3 layer with
+    input x (n, H, W, cin) and output gradient dy (n, H, W, cout) (CUDA tensors)."""
+    n, H, W, cin = x.shape
+    cout = dy.shape[-1]
+    rc = load().lbpf_nn_conv3x3_wgrad(_dptr(x), _dptr(dy), _dptr(dwt), n, H, W, cin, cout,
+                                      C.c_void_p(stream) if stream else None)
+    if rc != LBPF_OK:
+        raise LbpfError(rc, "lbpf_nn_conv3x3_wgrad failed")
 
 
 def nn_conv_error():

@@ -79,6 +79,37 @@ def test_conv_exact_on_dyadic_inputs(env):
     assert np.array_equal(y, yo)
 
 
+WG_SHAPES = [(2, 12, 20, 16, 32), (1, 16, 16, 384, 128), (1, 8, 16, 64, 256), (3, 5, 7, 48, 16), (4, 32, 32, 96, 32)]
+
+
+@pytest.mark.parametrize("shape", WG_SHAPES)
+def test_wgrad_matches_oracle(env, shape):
+    """Weight gradient, element by element against the oracle's BF16-operand
+    weight gradient: FP32 accumulation over K = n H W pixels (tensor core and
+    atomics in an unknown order) within gamma_K times the sum of the absolute
+    terms; the output starts from a non-zero dw (the call accumulates)."""
+    torch, U, L = env
+    n, H, W, cin, cout = shape
+    rng = np.random.default_rng(sum(shape))
+    x = rng.standard_normal((n, H, W, cin))
+    dy = rng.standard_normal((n, H, W, cout))
+    d0 = rng.standard_normal((9, cout, cin))
+    dw = torch.from_numpy(d0.astype(np.float32)).cuda()
+    L.nn_conv3x3_wgrad(torch.from_numpy(x.astype(np.float32)).cuda(), torch.from_numpy(dy.astype(np.float32)).cuda(),
+                       dw)
+    torch.cuda.synchronize()
+    assert L.nn_conv_error() == 0
+    got = dw.cpu().numpy().astype(np.float64)
+    want = d0.astype(np.float32).astype(np.float64) + U.conv3x3_wgrad(x, dy, emulate=True)
+    absum = np.abs(d0) + U.conv3x3_wgrad(np.abs(x), np.abs(dy), emulate=True)
+    K = n * H * W + 1
+    u = 2.0 ** -24
+    bar = K * u / (1 - K * u) * absum
+    err = np.abs(got - want)
+    print(f"wgrad {shape}: max |d dw| {err.max():.2e}, max / bound {(err / bar).max():.3f}")
+    assert np.all(err <= bar)
+
+
 def test_conv_rejects_bad_channels(env):
     torch, U, L = env
     x = torch.zeros((1, 8, 8, 24), device="cuda")
