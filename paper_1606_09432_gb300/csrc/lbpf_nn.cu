@@ -230,6 +230,132 @@ __global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restr
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
+// Halo variant of the same convolution for images whose H is a multiple of
+// 16 and W of 8: a block owns a 16 x 8 tile (M = 128: tile row = 8-row group,
+// pixel in the row = row of the core matrix), loads the 18 x 10 halo of all
+// cin channels once (FP32 -> BF16, layout [k8][halo pixel][8]), and every tap
+// is a descriptor over that halo: start at the tap's offset, SBO = one halo
+// row (10 pixels x 16 bytes), LBO = one 8-channel slice (180 x 16 bytes).
+// Only the weights stream through the two stage buffers (cp.async).
+constexpr int kHaloY = 18, kHaloX = 10, kHaloP = kHaloY * kHaloX;
+
+__global__ void __launch_bounds__(kConvM) conv3x3_halo_tc_kernel(const float* __restrict__ x,
+                                                                 const __nv_bfloat16* __restrict__ w,
+                                                                 const float* __restrict__ bias,
+                                                                 float* __restrict__ y, int H, int W, int cin,
+                                                                 int cout, int KC, int relu, uint32_t tmem_cols)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_x = W / 8, tiles = tiles_x * (H / 16);
+    const int img = blockIdx.x / tiles, t = blockIdx.x - img * tiles;
+    const int ty0 = (t / tiles_x) * 16, tx0 = (t % tiles_x) * 8;
+    const size_t halo_bytes = (size_t)kHaloP * cin * 2, b_bytes = (size_t)cout * KC * 2;
+    unsigned char* sH = smem_raw;
+    auto sB = [&](int b) { return smem_raw + halo_bytes + b * b_bytes; };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // halo: (pixel, 8-channel slice) pieces, FP32 -> BF16
+    const float* ximg = x + (size_t)img * H * W * cin;
+    const int k8n = cin / 8;
+    for (int e = tid; e < kHaloP * k8n; e += kConvM) {
+        const int hp = e / k8n, k8 = e - hp * k8n;
+        const int hy = hp / kHaloX, hx = hp - hy * kHaloX;
+        int gy = ty0 + hy - 1, gx = tx0 + hx - 1;
+        gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
+        gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
+        const float4* src = reinterpret_cast<const float4*>(ximg + ((size_t)gy * W + gx) * cin + 8 * k8);
+        const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
+        *reinterpret_cast<uint4*>(sH + ((size_t)k8 * kHaloP + hp) * 16) =
+            make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y), pack_bf16(f1.z, f1.w));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+
+    const int nkb = cin / KC, S = 9 * nkb;
+    const uint32_t idesc = umma_idesc_bf16(kConvM, cout);
+    const uint32_t h0 = smem_u32(sH);
+    bool ok = true;
+    int issued = 0;
+    for (int s = 0; s < S && ok; ++s) {
+        const int buf = s & 1, tap = s / nkb, c0 = (s - tap * nkb) * KC;
+        if (s >= 2 && !mbar_wait_bounded(&s_mbar[buf], ((s - 2) >> 1) & 1)) {
+            atomicOr(&g_conv_error, 16);
+            ok = false;
+            break;
+        }
+        for (int e = tid; e < cout * (KC / 8); e += kConvM) {
+            const int co = e % cout, k8 = e / cout;
+            const __nv_bfloat16* g = w + ((size_t)tap * cout + co) * cin + c0 + 8 * k8;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             smem_u32(sB(buf) + (size_t)k8 * cout * 16 + co * 16)),
+                         "l"(g));
+        }
+        asm volatile("cp.async.commit_group;");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const uint32_t tap_off = (uint32_t)(((1 + dy) * kHaloX + (1 + dx)) * 16);
+            const uint32_t b0 = smem_u32(sB(buf));
+            for (int k16 = 0; k16 < KC / 16; ++k16) {
+                const int k8 = c0 / 8 + 2 * k16;
+                const uint64_t ad = umma_desc(h0 + (uint32_t)k8 * kHaloP * 16 + tap_off, kHaloP * 16, kHaloX * 16);
+                const uint64_t bd = umma_desc(b0 + k16 * 2 * cout * 16, cout * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (s > 0 || k16 > 0) ? 1u : 0u);
+            }
+            umma_commit(&s_mbar[buf]);
+        }
+        issued = s + 1;
+    }
+    bool done = false;
+    if (issued > 0) {
+        const int last = issued - 1;
+        done = mbar_wait_bounded(&s_mbar[last & 1], (last >> 1) & 1);
+        if (!done) atomicOr(&g_conv_error, 32);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && done) {
+        const int m = tid, py = m >> 3, px = m & 7;
+        float* out = y + (((size_t)img * H + ty0 + py) * W + tx0 + px) * cout;
+        for (int c = 0; c < cout; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = __uint_as_float(r[j]) + (bias ? bias[c + j] : 0.f);
+                if (relu) v[j] = fmaxf(v[j], 0.f);
+            }
+            reinterpret_cast<float4*>(out + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<float4*>(out + c)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
 // Input channels a stage: all of them up to 64, else the largest of 64, 48,
 // 32, 16 dividing cin.
 static int conv_kc(int cin)
@@ -254,6 +380,22 @@ cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bia
     }
     uint32_t cols = 32;
     while ((int)cols < cout) cols <<= 1;
+    // halo tiles where the image divides into 16 x 8 tiles and the halo of
+    // all channels fits beside the two weight buffers
+    const size_t halo_smem = (size_t)kHaloP * cin * 2 + 2 * (size_t)cout * KC * 2;
+    if (H % 16 == 0 && W % 8 == 0 && halo_smem <= 200 * 1024) {
+        static int halo_attr = 0;
+        if ((int)halo_smem > halo_attr) {
+            cudaError_t e =
+                cudaFuncSetAttribute(conv3x3_halo_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)halo_smem);
+            if (e != cudaSuccess) return e;
+            halo_attr = (int)halo_smem;
+        }
+        const long long blocks = (long long)N * (H / 16) * (W / 8);
+        conv3x3_halo_tc_kernel<<<(unsigned)blocks, kConvM, halo_smem, s>>>(x, w, bias, y, H, W, cin, cout, KC, relu,
+                                                                           cols);
+        return cudaGetLastError();
+    }
     const long long P = (long long)N * H * W;
     const long long blocks = (P + kConvM - 1) / kConvM;
     conv3x3_tc_kernel<<<(unsigned)blocks, kConvM, smem, s>>>(x, w, bias, y, P, H, W, cin, cout, KC, relu, cols);

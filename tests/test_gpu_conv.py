@@ -7,7 +7,8 @@ tensor core chooses, against FP64.  Bar per element: the recursive-summation
 bound gamma_K = K u / (1 - K u), u = 2^-24, times the sum of the absolute
 terms, and the exact sum where every term is an exact multiple of 2^-20
 (sums of a few hundred such terms are exact in FP32 whatever the order).
-Shapes cover a partial last tile (pixels not a multiple of 128), several
+Two kernels: 16 x 8 halo tiles where H and W allow them, pixel gathers
+otherwise.  Shapes cover a partial last tile (pixels not a multiple of 128), several
 channel blocks a tap (cin 384 in blocks of 64, 96 in blocks of 48), the
 widest accumulator (cout 256), odd image sizes and both activations."""
 import numpy as np
@@ -15,8 +16,9 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 16, 24, 16, 16), (2, 12, 20, 32, 64), (1, 8, 8, 96, 32), (1, 16, 16, 384, 128), (1, 8, 16, 64, 256),
-          (3, 5, 7, 48, 16), (1, 1, 1, 16, 16)]
+# H a multiple of 16 and W of 8: the halo-tile kernel; otherwise the gather kernel
+SHAPES = [(1, 16, 24, 16, 16), (2, 32, 16, 32, 64), (1, 16, 8, 64, 256), (1, 48, 24, 96, 32), (1, 16, 16, 384, 128),
+          (2, 12, 20, 32, 64), (1, 8, 8, 96, 32), (1, 8, 16, 64, 256), (3, 5, 7, 48, 16), (1, 1, 1, 16, 16)]
 
 
 @pytest.fixture(scope="module")
@@ -65,13 +67,14 @@ def test_conv_matches_oracle(env, shape, relu):
     assert np.all(err <= bar + 1e-30)
 
 
-def test_conv_exact_on_dyadic_inputs(env):
+@pytest.mark.parametrize("shape", [(2, 9, 13, 64, 48), (2, 16, 16, 64, 48)])
+def test_conv_exact_on_dyadic_inputs(env, shape):
     """Inputs and weights multiples of 1/8 and 1/16 with small numerators:
     every partial sum is exact in FP32, so the tensor-core result must equal
-    the exact convolution bit for bit."""
+    the exact convolution bit for bit (gather and halo kernels)."""
     torch, U, L = env
     rng = np.random.default_rng(3)
-    n, H, W, cin, cout = 2, 9, 13, 64, 48
+    n, H, W, cin, cout = shape
     x = rng.integers(-8, 9, (n, H, W, cin)) / 8.0
     wq = rng.integers(-8, 9, (9, cout, cin)) / 16.0
     y = run(torch, L, x, wq, None, 0)
