@@ -297,7 +297,8 @@ def run_surrogate(args, size=1024):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     X, Y = S.generate_pairs(W.surrogate_draws(n_draws, size=train_size, seed=7), traj, K, torch)
-    net = L.Net(train_size, train_size, batch=8, seed=1)
+    arch = dict(levels=args.sur_levels, base=args.sur_base)
+    net = L.Net(train_size, train_size, batch=8, seed=1, **arch)
     net.set_loss_weight(alpha)
     hist = S.train(net, X, Y, args.sur_train, lr=1e-3, torch=torch)
     torch.cuda.synchronize()
@@ -306,7 +307,7 @@ def run_surrogate(args, size=1024):
     d["seeds"] = [(size / 2, size / 2, 0.0, 10.0, 0)]
     d["crystals"] = d["crystals"][:1]
     centre = (size // 2, size // 2, 0)
-    inf = L.Net(size, size, batch=1, seed=0)
+    inf = L.Net(size, size, batch=1, seed=0, **arch)
     inf.set_params(net.params())
 
     def solver():
@@ -345,7 +346,8 @@ def run_surrogate(args, size=1024):
             "config": {"workload": f"2D {size}^2 periodic, D2Q9/D2Q5 FP32, one seed R=10, {steps_total} steps, "
                                    f"K={K}, M={M}, k_v={kv}, network trained on {n_draws} draws at {train_size}^2 "
                                    f"({traj} LB steps each, pairs every K steps, {args.sur_train} Adam steps, "
-                                   f"interface loss weight {alpha})"},
+                                   f"interface loss weight {alpha}), U-Net {args.sur_levels} levels, "
+                                   f"base {args.sur_base} channels"},
             "plain_lb_s": round(t_plain, 4), "surrogate_lb_s": round(st.seconds, 4),
             "jumps_accepted": st.jumps_accepted, "blocks_rejected": st.blocks_rejected,
             "tip_velocity_rel_err": round(abs(v_sur - v_plain) / abs(v_plain), 4) if v_plain else None,
@@ -405,6 +407,8 @@ def main():
     ap.add_argument("--sur-train", type=int, default=1500, help="Adam steps")
     ap.add_argument("--sur-train-size", type=int, default=128, help="side of the training domains")
     ap.add_argument("--sur-steps", type=int, default=4400, help="LB steps to solution of the timed run")
+    ap.add_argument("--sur-levels", type=int, default=3, help="U-Net levels")
+    ap.add_argument("--sur-base", type=int, default=16, help="U-Net channels at the top level")
     ap.add_argument("--replicate", choices=["sec42", "sec52", "all"],
                     help="paper-scale isotropy runs of Secs. 4.2 / 5.2 instead of the benchmark")
     ap.add_argument("--rep-steps", type=int, default=0, help="steps of the Sec. 4.2 run (default 1e5)")

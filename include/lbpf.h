@@ -372,21 +372,29 @@ int lbpf_field_sums_static(const void* phi, const void* u, long long n, int prec
  * Learned surrogate (not in the paper): a 2D U-Net that predicts the change
  * of phi and u over a jump of K lattice Boltzmann steps, used by a controller
  * that alternates network jumps with plain LB validation and falls back to LB.
- * Architecture: three levels of two periodic 3x3 convolutions + ReLU (16, 32,
- * 64 channels), 2x2 average pooling, nearest 2x upsampling with skip
- * concatenation, 1x1 head to 2 channels.  Input per site (NHWC, FP32):
- * (phi, u, cos 4 theta, sin 4 theta, eps); output (d phi, d u), the phi
+ * Architecture: `levels` levels with base * 2^l channels at level l (default
+ * 3 levels, base 16: 16, 32, 64 channels), two periodic 3x3 convolutions +
+ * ReLU per level on the way down (2x2 average pooling between levels) and on
+ * the way up (nearest 2x upsampling concatenated with the level's skip), 1x1
+ * head to 2 channels.  Input per site (NHWC, FP32): (phi, u, cos 4 theta,
+ * sin 4 theta, eps) zero-padded to 16 channels; output (d phi, d u), the phi
  * channel multiplied by (1 - phi^2) so that the bulk phases stay fixed.  3x3
- * convolutions run on the tensor cores with BF16 operands (weights and
- * staged activations) and FP32 accumulation; everything else in FP32.
- * Parameters: one flat FP32 vector (per 3x3 layer weights [tap][cout][cin]
- * then biases, then the head's [2][16] weights and 2 biases).
+ * convolutions and their weight gradients run on the tensor cores (tcgen05,
+ * BF16 operands, FP32 accumulation); everything else in FP32.
+ * Parameters: one flat FP32 vector (per 3x3 layer, encoder level by level
+ * then decoder from the deepest level up: weights [tap][cout][cin], then
+ * biases; then the head's [2][base] weights and 2 biases).
  * All device pointers below are device memory of the current GPU.
  * ------------------------------------------------------------------------- */
 typedef struct lbpf_net lbpf_net;
 
-/* Network for batches of `batch` images of H x W sites (H, W multiples of
- * 32), He-uniform weights from `seed`.  Errors: LBPF_EINVAL, LBPF_ENOMEM. */
+/* Network for batches of `batch` images of H x W sites, He-uniform weights
+ * from `seed`: levels 2..5, base 16, 32 or 64 with base 2^(levels - 1) <=
+ * 256; H, W multiples of 8 * 2^(levels - 1).  Errors: LBPF_EINVAL,
+ * LBPF_ENOMEM, LBPF_ECUDA. */
+int lbpf_net_create_arch(int H, int W, int batch, int levels, int base, unsigned long long seed, void* stream,
+                         lbpf_net** out);
+/* The default network: lbpf_net_create_arch with 3 levels, base 16. */
 int lbpf_net_create(int H, int W, int batch, unsigned long long seed, void* stream, lbpf_net** out);
 int lbpf_net_destroy(lbpf_net* net);
 const char* lbpf_net_last_error(const lbpf_net* net);
@@ -433,8 +441,10 @@ int lbpf_net_range_check(const float* phi, long long sites, float lo, float hi, 
  * FP32 (n, H, W, cout); wt: BF16 bit patterns [9][cout][cin]; bias: FP32
  * [cout] or NULL.  x is rounded to BF16 (to nearest even) on the way in.
  * All pointers are device memory owned by the caller; the call is
- * asynchronous on `stream`.  cin and cout multiples of 16, cout <= 256,
- * n, H, W >= 1: else LBPF_EINVAL; LBPF_ECUDA if the launch fails. */
+ * asynchronous on `stream`.  cin a multiple of 16; cout split into equal
+ * tiles of at most 256 channels (one MMA), each a multiple of 16 (so cout
+ * above 256 a multiple of 32, above 512 of 48); n, H, W >= 1: else
+ * LBPF_EINVAL; LBPF_ECUDA if the launch fails. */
 int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias, float* y, int n, int H, int W, int cin,
                     int cout, int relu, void* stream);
 /* Weight gradient of that layer, added to dwt:

@@ -1,10 +1,14 @@
 """FP64 NumPy oracle of the learned surrogate's U-Net (test infrastructure).
 
 Same architecture and flat parameter layout as the CUDA network
-(include/lbpf.h, "Learned surrogate"): three levels of two periodic 3x3
-convolutions + ReLU (16, 32, 64 channels), 2x2 average pooling, nearest 2x
-upsampling with skip concatenation, 1x1 head to 2 channels whose phi channel
-is gated by (1 - phi^2); input (N, H, W, 5) zero-padded to 16 channels.  The
+(include/lbpf.h, "Learned surrogate"): a U-Net of `levels` levels with
+base * 2^l channels at level l, two periodic 3x3 convolutions + ReLU per
+level on the way down (2x2 average pooling between levels) and on the way up
+(nearest 2x upsampling, concatenated with the level's skip), a 1x1 head to 2
+channels whose phi channel is gated by (1 - phi^2); input (N, H, W, 5)
+zero-padded to 16 channels.  The default (3 levels, base 16) has channels
+16, 32, 64.  Layer order: the encoder's convolutions level by level, then the
+decoder's from the deepest level up.  The
 backward pass is written out layer by layer (plain chain rule).  With
 emulate=True the operands of every 3x3 convolution
 (weights, and the activations or gradients it reads) are rounded to BF16
@@ -18,27 +22,43 @@ from __future__ import annotations
 
 import numpy as np
 
-LAYERS = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
 N_IN, N_IN_PAD, N_OUT = 5, 16, 2
+ARCH = (3, 16)  # (levels, base channels) of the default network
 
 
-def n_params():
-    return sum(9 * ci * co + co for ci, co in LAYERS) + N_OUT * 16 + N_OUT
+def layers(arch=ARCH):
+    """(cin, cout) of the 3x3 convolutions in order."""
+    lv, base = arch
+    c = [base << l for l in range(lv)]
+    out = [(N_IN_PAD, c[0]), (c[0], c[0])]
+    for l in range(1, lv):
+        out += [(c[l - 1], c[l]), (c[l], c[l])]
+    for l in range(lv - 2, -1, -1):
+        out += [(c[l + 1] + c[l], c[l]), (c[l], c[l])]
+    return out
 
 
-def unpack(p):
+LAYERS = layers()
+
+
+def n_params(arch=ARCH):
+    return sum(9 * ci * co + co for ci, co in layers(arch)) + N_OUT * arch[1] + N_OUT
+
+
+def unpack(p, arch=ARCH):
     """Flat vector -> list of (W[tap][co][ci], b[co]) for the 3x3 layers, and
     the head (W[co][ci], b[co])."""
     p = np.asarray(p, dtype=np.float64)
     out, k = [], 0
-    for ci, co in LAYERS:
+    for ci, co in layers(arch):
         w = p[k:k + 9 * ci * co].reshape(9, co, ci)
         k += 9 * ci * co
         b = p[k:k + co]
         k += co
         out.append((w, b))
-    hw = p[k:k + N_OUT * 16].reshape(N_OUT, 16)
-    k += N_OUT * 16
+    c0 = arch[1]
+    hw = p[k:k + N_OUT * c0].reshape(N_OUT, c0)
+    k += N_OUT * c0
     hb = p[k:k + N_OUT]
     return out, (hw, hb)
 
@@ -116,35 +136,41 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(p, x, emulate=False):
-    """Returns (out, cache)."""
-    L, (hw, hb) = unpack(p)
+def forward(p, x, emulate=False, arch=ARCH):
+    """Returns (out, cache).  Cache: the input, per encoder level l the
+    convolution outputs ("ea", l), ("e", l) and the pooled input ("p", l)
+    (l >= 1), per decoder level the concatenation ("u", l) and the outputs
+    ("da", l), ("d", l)."""
+    lv = arch[0]
+    L, (hw, hb) = unpack(p, arch)
     xin = np.concatenate([x, np.zeros(x.shape[:3] + (N_IN_PAD - x.shape[3],))], axis=3)
     c = {"xin": xin}
     cv = lambda k, a: relu(conv3x3(a, L[k][0], L[k][1], emulate))
-    c["a1a"] = cv(0, xin)
-    c["a1"] = cv(1, c["a1a"])
-    c["p1"] = pool(c["a1"])
-    c["a2a"] = cv(2, c["p1"])
-    c["a2"] = cv(3, c["a2a"])
-    c["p2"] = pool(c["a2"])
-    c["a3a"] = cv(4, c["p2"])
-    c["a3"] = cv(5, c["a3a"])
-    c["u2"] = np.concatenate([up(c["a3"]), c["a2"]], axis=3)
-    c["d2a"] = cv(6, c["u2"])
-    c["d2"] = cv(7, c["d2a"])
-    c["u1"] = np.concatenate([up(c["d2"]), c["a1"]], axis=3)
-    c["d1a"] = cv(8, c["u1"])
-    c["d1"] = cv(9, c["d1a"])
-    out = c["d1"] @ hw.T + hb
+    k = 0
+    a = xin
+    for l in range(lv):
+        if l > 0:
+            a = c[("p", l)] = pool(c[("e", l - 1)])
+        c[("ea", l)] = cv(k, a)
+        c[("e", l)] = cv(k + 1, c[("ea", l)])
+        k += 2
+    prev = c[("e", lv - 1)]
+    for l in range(lv - 2, -1, -1):
+        c[("u", l)] = np.concatenate([up(prev), c[("e", l)]], axis=3)
+        c[("da", l)] = cv(k, c[("u", l)])
+        prev = c[("d", l)] = cv(k + 1, c[("da", l)])
+        k += 2
+    out = prev @ hw.T + hb
     out[..., 0] *= 1.0 - xin[..., 0] ** 2  # interface gate of the phi output
+    c["top"] = prev
     return out, c
 
 
-def backward(p, c, dout, emulate=False):
+def backward(p, c, dout, emulate=False, arch=ARCH):
     """Gradient of sum(out * dout) with respect to the flat parameter vector."""
-    L, (hw, hb) = unpack(p)
-    grads = [None] * len(LAYERS)
+    lv, base = arch
+    L, (hw, hb) = unpack(p, arch)
+    grads = [None] * len(L)
     dout = dout.copy()
     dout[..., 0] *= 1.0 - c["xin"][..., 0] ** 2
 
@@ -153,23 +179,27 @@ def backward(p, c, dout, emulate=False):
         grads[k] = (conv3x3_wgrad(a_in, dy, emulate), dy.sum(axis=(0, 1, 2)))
         return conv3x3_dgrad(dy, L[k][0], emulate) if need_dx else None
 
-    ghw = np.einsum("nhwo,nhwi->oi", dout, c["d1"])
+    ghw = np.einsum("nhwo,nhwi->oi", dout, c["top"])
     ghb = dout.sum(axis=(0, 1, 2))
     g = dout @ hw
-    g = cvb(9, c["d1a"], c["d1"], g)
-    g = cvb(8, c["u1"], c["d1a"], g)
-    g_d2, g_a1 = up_bwd(g[..., :32]), g[..., 32:]
-    g = cvb(7, c["d2a"], c["d2"], g_d2)
-    g = cvb(6, c["u2"], c["d2a"], g)
-    g_a3, g_a2 = up_bwd(g[..., :64]), g[..., 64:]
-    g = cvb(5, c["a3a"], c["a3"], g_a3)
-    g = cvb(4, c["p2"], c["a3a"], g)
-    g_a2 = g_a2 + pool_bwd(g)
-    g = cvb(3, c["a2a"], c["a2"], g_a2)
-    g = cvb(2, c["p1"], c["a2a"], g)
-    g_a1 = g_a1 + pool_bwd(g)
-    g = cvb(1, c["a1a"], c["a1"], g_a1)
-    cvb(0, c["xin"], c["a1a"], g, need_dx=False)
+    k = len(L)
+    skip = {}
+    for l in range(0, lv - 1):  # decoder, from the top level down
+        k -= 2
+        g = cvb(k + 1, c[("da", l)], c[("d", l)], g)
+        g = cvb(k, c[("u", l)], c[("da", l)], g)
+        cu = base << (l + 1)
+        skip[l] = g[..., cu:]
+        g = up_bwd(g[..., :cu])  # gradient of the level l + 1 output
+    for l in range(lv - 1, -1, -1):  # encoder, from the deepest level up
+        k -= 2
+        if l < lv - 1:
+            g = g + skip[l]
+        g = cvb(k + 1, c[("ea", l)], c[("e", l)], g)
+        g = cvb(k, c[("p", l)] if l > 0 else c["xin"], c[("ea", l)], g, need_dx=l > 0)
+        if l > 0:
+            g = pool_bwd(g)
+    assert k == 0
     flat = []
     for dw, db in grads:
         flat += [dw.ravel(), db]
@@ -187,11 +217,11 @@ def weighted_mse(out, target, x, alpha=0.0):
     return float((w * d * d).sum() / n), 2.0 * w * d / n
 
 
-def init_params(seed, scale_head=1e-2):
+def init_params(seed, scale_head=1e-2, arch=ARCH):
     rng = np.random.default_rng(seed)
     parts = []
-    for ci, co in LAYERS:
+    for ci, co in layers(arch):
         a = np.sqrt(6.0 / (9 * ci))
         parts += [rng.uniform(-a, a, 9 * co * ci), np.zeros(co)]
-    parts += [rng.uniform(-scale_head, scale_head, N_OUT * 16), np.zeros(N_OUT)]
+    parts += [rng.uniform(-scale_head, scale_head, N_OUT * arch[1]), np.zeros(N_OUT)]
     return np.concatenate(parts)

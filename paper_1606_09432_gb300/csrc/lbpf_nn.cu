@@ -107,9 +107,11 @@ constexpr int kConvM = 128;  // pixels per block (one TMEM lane each)
 __global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restrict__ x,
                                                             const __nv_bfloat16* __restrict__ w,
                                                             const float* __restrict__ bias, float* __restrict__ y,
-                                                            long long P, int H, int W, int cin, int cout, int KC,
-                                                            int relu, uint32_t tmem_cols)
+                                                            long long P, int H, int W, int cin, int cout_all,
+                                                            int cout, int KC, int relu, uint32_t tmem_cols)
 {
+    // output channels co0 .. co0 + cout of cout_all (grid y: channel tile)
+    const int co0 = blockIdx.y * cout;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar[2];
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restr
         // B: 16-byte pieces w[tap][co][c0 + 8 k8 ..] -> [k8][co]
         for (int e = tid; e < cout * (KC / 8); e += kConvM) {
             const int co = e % cout, k8 = e / cout;
-            const __nv_bfloat16* g = w + ((size_t)tap * cout + co) * cin + c0 + 8 * k8;
+            const __nv_bfloat16* g = w + ((size_t)tap * cout_all + co0 + co) * cin + c0 + 8 * k8;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                              smem_u32(sB(buf) + (size_t)k8 * cout * 16 + co * 16)),
                          "l"(g));
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restr
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && done) {
-        float* out = y + p * cout;
+        float* out = y + p * cout_all + co0;
         for (int c = 0; c < cout; c += 8) {
             uint32_t r[8];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_tc_kernel(const float* __restr
                 float v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    v[j] = __uint_as_float(r[j]) + (bias ? bias[c + j] : 0.f);
+                    v[j] = __uint_as_float(r[j]) + (bias ? bias[co0 + c + j] : 0.f);
                     if (relu) v[j] = fmaxf(v[j], 0.f);
                 }
                 reinterpret_cast<float4*>(out + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -243,8 +245,10 @@ __global__ void __launch_bounds__(kConvM) conv3x3_halo_tc_kernel(const float* __
                                                                  const __nv_bfloat16* __restrict__ w,
                                                                  const float* __restrict__ bias,
                                                                  float* __restrict__ y, int H, int W, int cin,
-                                                                 int cout, int KC, int relu, uint32_t tmem_cols)
+                                                                 int cout_all, int cout, int KC, int relu,
+                                                                 uint32_t tmem_cols)
 {
+    const int co0 = blockIdx.y * cout;  // output channel tile
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar[2];
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_halo_tc_kernel(const float* __
         }
         for (int e = tid; e < cout * (KC / 8); e += kConvM) {
             const int co = e % cout, k8 = e / cout;
-            const __nv_bfloat16* g = w + ((size_t)tap * cout + co) * cin + c0 + 8 * k8;
+            const __nv_bfloat16* g = w + ((size_t)tap * cout_all + co0 + co) * cin + c0 + 8 * k8;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                              smem_u32(sB(buf) + (size_t)k8 * cout * 16 + co * 16)),
                          "l"(g));
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_halo_tc_kernel(const float* __
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && done) {
         const int m = tid, py = m >> 3, px = m & 7;
-        float* out = y + (((size_t)img * H + ty0 + py) * W + tx0 + px) * cout;
+        float* out = y + (((size_t)img * H + ty0 + py) * W + tx0 + px) * cout_all + co0;
         for (int c = 0; c < cout; c += 8) {
             uint32_t r[8];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_halo_tc_kernel(const float* __
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                v[j] = __uint_as_float(r[j]) + (bias ? bias[c + j] : 0.f);
+                v[j] = __uint_as_float(r[j]) + (bias ? bias[co0 + c + j] : 0.f);
                 if (relu) v[j] = fmaxf(v[j], 0.f);
             }
             reinterpret_cast<float4*>(out + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -367,9 +371,13 @@ static int conv_kc(int cin)
 }
 
 cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int N, int H, int W,
-                        int cin, int cout, int relu, cudaStream_t s)
+                        int cin, int cout_all, int relu, cudaStream_t s)
 {
-    if (cin % 16 || cout % 16 || cin < 16 || cout < 16 || cout > 256 || H < 1 || W < 1) return cudaErrorInvalidValue;
+    // output channels in equal tiles of at most 256 (one MMA's N), multiples of 16
+    const int n_tiles = (cout_all + 255) / 256;
+    if (cin % 16 || cout_all % (16 * n_tiles) || cin < 16 || cout_all < 16 || H < 1 || W < 1)
+        return cudaErrorInvalidValue;
+    const int cout = cout_all / n_tiles;
     const int KC = conv_kc(cin);
     const size_t smem = 2 * ((size_t)kConvM * KC * 2 + (size_t)cout * KC * 2);
     static int attr_bytes = 0;
@@ -392,13 +400,15 @@ cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bia
             halo_attr = (int)halo_smem;
         }
         const long long blocks = (long long)N * (H / 16) * (W / 8);
-        conv3x3_halo_tc_kernel<<<(unsigned)blocks, kConvM, halo_smem, s>>>(x, w, bias, y, H, W, cin, cout, KC, relu,
-                                                                           cols);
+        conv3x3_halo_tc_kernel<<<dim3((unsigned)blocks, n_tiles), kConvM, halo_smem, s>>>(x, w, bias, y, H, W, cin,
+                                                                                          cout_all, cout, KC, relu,
+                                                                                          cols);
         return cudaGetLastError();
     }
     const long long P = (long long)N * H * W;
     const long long blocks = (P + kConvM - 1) / kConvM;
-    conv3x3_tc_kernel<<<(unsigned)blocks, kConvM, smem, s>>>(x, w, bias, y, P, H, W, cin, cout, KC, relu, cols);
+    conv3x3_tc_kernel<<<dim3((unsigned)blocks, n_tiles), kConvM, smem, s>>>(x, w, bias, y, P, H, W, cin, cout_all,
+                                                                            cout, KC, relu, cols);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@
 namespace lbpf_nn {
 
 // y = act(conv3x3(x, w) + bias), periodic padding, on the tensor cores
-// (tcgen05); cin, cout multiples of 16, cout <= 256.  w: BF16 [tap][cout][cin].
+// (tcgen05); cin a multiple of 16; cout in equal tiles of at most 256
+// channels, each a multiple of 16.  w: BF16 [tap][cout][cin].
 cudaError_t conv3x3_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int N, int H, int W,
                         int cin, int cout, int relu, cudaStream_t s);
 // Error word of the convolution kernels (1, 2: a bounded wait of a block

@@ -1,10 +1,13 @@
-// The learned surrogate's network runtime: a 2D U-Net with three levels
-// (16, 32, 64 channels), periodic 3x3 convolutions + ReLU, 2x2 average
-// pooling, nearest 2x upsampling with skip concatenation and a 1x1 head.
+// The learned surrogate's network runtime: a 2D U-Net of `levels` levels
+// with base * 2^l channels at level l (default 3 levels, base 16: 16, 32, 64
+// channels), two periodic 3x3 convolutions + ReLU per level on the way down
+// (2x2 average pooling between levels) and on the way up (nearest 2x
+// upsampling concatenated with the level's skip), and a 1x1 head.
 // Input per site: (phi, u, cos 4 theta, sin 4 theta, eps) zero-padded to 16
 // channels; output: (d phi, d u), the change of phi and u over the jump, the
 // phi channel gated by (1 - phi^2) so that the bulk phases stay untouched.
-// Forward, hand-written backward and Adam run in the kernels of lbpf_nn.cu.
+// Forward, hand-written backward and Adam run in the kernels of lbpf_nn.cu
+// (3x3 convolutions and their weight gradients on the tensor cores).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -31,20 +34,29 @@ struct Conv {
 }  // namespace
 
 struct lbpf_net {
-    int H = 0, W = 0, N = 0;
+    int H = 0, W = 0, N = 0, levels = 3, base = 16;
     cudaStream_t stream = nullptr;
-    std::vector<Conv> conv;  // 10 3x3 convolutions in forward order
+    std::vector<Conv> conv;  // 4 levels - 2 3x3 convolutions: encoder level by level, then decoder top-down
     long long off_hw = 0, off_hb = 0, n_params = 0;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 params, grads, Adam moments
-    __nv_bfloat16* pb = nullptr;  // BF16 copy of all params (only 3x3 parts used)
+    __nv_bfloat16* pb = nullptr;  // BF16 copies of the 3x3 weights and their flipped forms
     int adam_t = 0;
     float loss_alpha = 0.f;  // interface weight of the training loss
-    // activations (N, h, w, c) and their gradients
-    float *xin, *a1a, *a1, *p1, *a2a, *a2, *p2, *a3a, *a3, *u2, *d2a, *d2, *u1, *d1a, *d1, *out;
-    float *g_big0, *g_big1, *g_mid0, *g_mid1, *g_sml0, *g_sml1, *g_cat1, *g_cat2, *g_out;
+    // activations (N, H >> l, W >> l, c) per level l: encoder convolution
+    // outputs ea, e; pooled input pl (l >= 1); decoder concatenation u and
+    // outputs da, d (l < levels - 1)
+    float *xin = nullptr, *out = nullptr;
+    std::vector<float*> ea, e, pl, u, da, d;
+    // gradient scratch per level (two of the level's widest channel count)
+    // and the skip gradients of the decoder levels
+    std::vector<float*> ga, gb, gskip;
+    float* g_out = nullptr;
     double* d_loss = nullptr;
     std::vector<void*> allocs;
     std::string err;
+
+    int ch(int l) const { return base << l; }
+    float* top() const { return levels > 1 ? d[0] : e[0]; }
 };
 
 namespace {
@@ -69,12 +81,12 @@ int net_fail(lbpf_net* n, int code, const char* msg)
 float* alloc_f(lbpf_net* net, long long n)
 {
     void* p = nullptr;
-    if (cudaMalloc(&p, sizeof(float) * (size_t)n) != cudaSuccess) {
+    if (cudaMalloc(&p, sizeof(float) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     net->allocs.push_back(p);
-    cudaMemsetAsync(p, 0, sizeof(float) * (size_t)n, net->stream);
+    cudaMemsetAsync(p, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), net->stream);
     return static_cast<float*>(p);
 }
 
@@ -103,41 +115,56 @@ int refresh_bf16(lbpf_net* net)
 
 }  // namespace
 
-extern "C" int lbpf_net_create(int H, int W, int batch, unsigned long long seed, void* stream, lbpf_net** out)
+extern "C" int lbpf_net_create_arch(int H, int W, int batch, int levels, int base, unsigned long long seed,
+                                    void* stream, lbpf_net** out)
 {
     if (!out) return net_fail(nullptr, LBPF_EINVAL, "lbpf_net_create: out is NULL");
     *out = nullptr;
-    if (H < 32 || W < 32 || H % 32 || W % 32 || batch < 1)
-        return net_fail(nullptr, LBPF_EINVAL, "lbpf_net_create: H, W must be multiples of 32 (>= 32), batch >= 1");
+    if (levels < 2 || levels > 5 || !(base == 16 || base == 32 || base == 64) || (base << (levels - 1)) > 256)
+        return net_fail(nullptr, LBPF_EINVAL,
+                        "lbpf_net_create: levels 2..5, base 16, 32 or 64, at most 256 channels at the deepest level");
+    const int q = 8 << (levels - 1);
+    if (H < q || W < q || H % q || W % q || batch < 1)
+        return net_fail(nullptr, LBPF_EINVAL, "lbpf_net_create: H, W must be multiples of 8 * 2^(levels - 1), batch >= 1");
     lbpf_net* net = new (std::nothrow) lbpf_net();
     if (!net) return net_fail(nullptr, LBPF_ENOMEM, "lbpf_net_create: out of host memory");
     net->H = H;
     net->W = W;
     net->N = batch;
+    net->levels = levels;
+    net->base = base;
     net->stream = static_cast<cudaStream_t>(stream);
-    const int cfg[10][2] = {{16, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64}, {96, 32}, {32, 32}, {48, 16}, {16, 16}};
-    long long off = 0;
+    std::vector<std::pair<int, int>> cfg = {{kInPad, net->ch(0)}, {net->ch(0), net->ch(0)}};
+    for (int l = 1; l < levels; ++l) {
+        cfg.push_back({net->ch(l - 1), net->ch(l)});
+        cfg.push_back({net->ch(l), net->ch(l)});
+    }
+    for (int l = levels - 2; l >= 0; --l) {
+        cfg.push_back({net->ch(l + 1) + net->ch(l), net->ch(l)});
+        cfg.push_back({net->ch(l), net->ch(l)});
+    }
+    long long off = 0, wtot = 0;
     for (auto& c2 : cfg) {
         Conv c;
-        c.cin = c2[0];
-        c.cout = c2[1];
+        c.cin = c2.first;
+        c.cout = c2.second;
         c.off_w = off;
         off += 9LL * c.cin * c.cout;
+        wtot += 9LL * c.cin * c.cout;
         c.off_b = off;
         off += c.cout;
         net->conv.push_back(c);
     }
     net->off_hw = off;
-    off += kOut * 16;
+    off += kOut * net->ch(0);
     net->off_hb = off;
     off += kOut;
     net->n_params = off;
 
-    const long long P1 = (long long)batch * H * W, P2 = P1 / 4, P3 = P1 / 16;
     bool ok = (net->p = alloc_f(net, off)) && (net->g = alloc_f(net, off)) && (net->m = alloc_f(net, off)) &&
               (net->v = alloc_f(net, off));
     void* pb = nullptr;
-    ok = ok && cudaMalloc(&pb, sizeof(__nv_bfloat16) * (size_t)off * 2) == cudaSuccess;
+    ok = ok && cudaMalloc(&pb, sizeof(__nv_bfloat16) * (size_t)wtot * 2) == cudaSuccess;
     if (pb) net->allocs.push_back(pb);
     if (ok) {
         net->pb = static_cast<__nv_bfloat16*>(pb);
@@ -149,17 +176,28 @@ extern "C" int lbpf_net_create(int H, int W, int batch, unsigned long long seed,
             cur += 9LL * c.cin * c.cout;
         }
     }
-    ok = ok && (net->xin = alloc_f(net, P1 * kInPad)) && (net->a1a = alloc_f(net, P1 * 16)) &&
-         (net->a1 = alloc_f(net, P1 * 16)) && (net->p1 = alloc_f(net, P2 * 16)) && (net->a2a = alloc_f(net, P2 * 32)) &&
-         (net->a2 = alloc_f(net, P2 * 32)) && (net->p2 = alloc_f(net, P3 * 32)) && (net->a3a = alloc_f(net, P3 * 64)) &&
-         (net->a3 = alloc_f(net, P3 * 64)) && (net->u2 = alloc_f(net, P2 * 96)) && (net->d2a = alloc_f(net, P2 * 32)) &&
-         (net->d2 = alloc_f(net, P2 * 32)) && (net->u1 = alloc_f(net, P1 * 48)) && (net->d1a = alloc_f(net, P1 * 16)) &&
-         (net->d1 = alloc_f(net, P1 * 16)) && (net->out = alloc_f(net, P1 * kOut));
-    ok = ok && (net->g_big0 = alloc_f(net, P1 * 16)) && (net->g_big1 = alloc_f(net, P1 * 16)) &&
-         (net->g_mid0 = alloc_f(net, P2 * 32)) && (net->g_mid1 = alloc_f(net, P2 * 32)) &&
-         (net->g_sml0 = alloc_f(net, P3 * 64)) && (net->g_sml1 = alloc_f(net, P3 * 64)) &&
-         (net->g_cat1 = alloc_f(net, P1 * 48)) && (net->g_cat2 = alloc_f(net, P2 * 96)) &&
-         (net->g_out = alloc_f(net, P1 * kOut));
+    const long long P0 = (long long)batch * H * W;
+    net->ea.assign(levels, nullptr);
+    net->e.assign(levels, nullptr);
+    net->pl.assign(levels, nullptr);
+    net->u.assign(levels, nullptr);
+    net->da.assign(levels, nullptr);
+    net->d.assign(levels, nullptr);
+    net->ga.assign(levels, nullptr);
+    net->gb.assign(levels, nullptr);
+    net->gskip.assign(levels, nullptr);
+    ok = ok && (net->xin = alloc_f(net, P0 * kInPad)) && (net->out = alloc_f(net, P0 * kOut)) &&
+         (net->g_out = alloc_f(net, P0 * kOut));
+    for (int l = 0; l < levels && ok; ++l) {
+        const long long Pl = P0 >> (2 * l);
+        const int c = net->ch(l), cw = l + 1 < levels ? c + net->ch(l + 1) : c;
+        ok = (net->ea[l] = alloc_f(net, Pl * c)) && (net->e[l] = alloc_f(net, Pl * c)) &&
+             (net->ga[l] = alloc_f(net, Pl * cw)) && (net->gb[l] = alloc_f(net, Pl * cw));
+        if (ok && l > 0) ok = (net->pl[l] = alloc_f(net, Pl * net->ch(l - 1))) != nullptr;
+        if (ok && l + 1 < levels)
+            ok = (net->u[l] = alloc_f(net, Pl * cw)) && (net->da[l] = alloc_f(net, Pl * c)) &&
+                 (net->d[l] = alloc_f(net, Pl * c)) && (net->gskip[l] = alloc_f(net, Pl * c));
+    }
     void* dl = nullptr;
     ok = ok && cudaMalloc(&dl, sizeof(double)) == cudaSuccess;
     if (dl) {
@@ -168,7 +206,7 @@ extern "C" int lbpf_net_create(int H, int W, int batch, unsigned long long seed,
     }
     if (!ok) {
         cudaGetLastError();
-        for (void* q : net->allocs) cudaFree(q);
+        for (void* q2 : net->allocs) cudaFree(q2);
         delete net;
         return net_fail(nullptr, LBPF_ENOMEM, "lbpf_net_create: device allocation failed");
     }
@@ -179,17 +217,22 @@ extern "C" int lbpf_net_create(int H, int W, int batch, unsigned long long seed,
         const double a = std::sqrt(6.0 / (9.0 * c.cin));
         for (long long k = 0; k < 9LL * c.cin * c.cout; ++k) h[c.off_w + k] = (float)((2 * rng.uniform() - 1) * a);
     }
-    for (int k = 0; k < kOut * 16; ++k) h[net->off_hw + k] = (float)((2 * rng.uniform() - 1) * 1e-2);
+    for (int k = 0; k < kOut * net->ch(0); ++k) h[net->off_hw + k] = (float)((2 * rng.uniform() - 1) * 1e-2);
     if (cudaMemcpyAsync(net->p, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, net->stream) !=
             cudaSuccess ||
         refresh_bf16(net) != LBPF_OK || cudaStreamSynchronize(net->stream) != cudaSuccess) {
         cudaGetLastError();
-        for (void* q : net->allocs) cudaFree(q);
+        for (void* q2 : net->allocs) cudaFree(q2);
         delete net;
         return net_fail(nullptr, LBPF_ECUDA, "lbpf_net_create: initialisation failed");
     }
     *out = net;
     return LBPF_OK;
+}
+
+extern "C" int lbpf_net_create(int H, int W, int batch, unsigned long long seed, void* stream, lbpf_net** out)
+{
+    return lbpf_net_create_arch(H, W, batch, 3, 16, seed, stream, out);
 }
 
 extern "C" int lbpf_net_destroy(lbpf_net* net)
@@ -233,43 +276,52 @@ namespace {
 
 int forward(lbpf_net* net, const float* x)
 {
-    const int N = net->N, H = net->H, W = net->W;
-    const long long P1 = (long long)N * H * W;
+    const int N = net->N, H = net->H, W = net->W, lv = net->levels;
+    const long long P0 = (long long)N * H * W;
     cudaStream_t s = net->stream;
-    auto cv = [&](int k, const float* in, float* o, int h, int w) -> cudaError_t {
+    auto cv = [&](int k, const float* in, float* o, int l) -> cudaError_t {
         const Conv& c = net->conv[k];
-        return conv3x3_fwd(in, c.wb, net->p + c.off_b, o, N, h, w, c.cin, c.cout, 1, s);
+        return conv3x3_fwd(in, c.wb, net->p + c.off_b, o, N, H >> l, W >> l, c.cin, c.cout, 1, s);
     };
-    NK(pad_channels(x, net->xin, P1, kIn, kInPad, s));
-    NK(cv(0, net->xin, net->a1a, H, W));
-    NK(cv(1, net->a1a, net->a1, H, W));
-    NK(pool_fwd(net->a1, net->p1, N, H, W, 16, s));
-    NK(cv(2, net->p1, net->a2a, H / 2, W / 2));
-    NK(cv(3, net->a2a, net->a2, H / 2, W / 2));
-    NK(pool_fwd(net->a2, net->p2, N, H / 2, W / 2, 32, s));
-    NK(cv(4, net->p2, net->a3a, H / 4, W / 4));
-    NK(cv(5, net->a3a, net->a3, H / 4, W / 4));
-    NK(upcat_fwd(net->a3, net->a2, net->u2, N, H / 2, W / 2, 64, 32, s));
-    NK(cv(6, net->u2, net->d2a, H / 2, W / 2));
-    NK(cv(7, net->d2a, net->d2, H / 2, W / 2));
-    NK(upcat_fwd(net->d2, net->a1, net->u1, N, H, W, 32, 16, s));
-    NK(cv(8, net->u1, net->d1a, H, W));
-    NK(cv(9, net->d1a, net->d1, H, W));
-    NK(conv1x1_fwd(net->d1, net->p + net->off_hw, net->p + net->off_hb, net->out, P1, 16, kOut, s));
-    NK(gate(net->xin, kInPad, net->out, P1, s));
+    NK(pad_channels(x, net->xin, P0, kIn, kInPad, s));
+    int k = 0;
+    for (int l = 0; l < lv; ++l) {
+        const float* a = net->xin;
+        if (l > 0) {
+            NK(pool_fwd(net->e[l - 1], net->pl[l], N, H >> (l - 1), W >> (l - 1), net->ch(l - 1), s));
+            a = net->pl[l];
+        }
+        NK(cv(k, a, net->ea[l], l));
+        NK(cv(k + 1, net->ea[l], net->e[l], l));
+        k += 2;
+    }
+    const float* prev = net->e[lv - 1];
+    for (int l = lv - 2; l >= 0; --l) {
+        NK(upcat_fwd(prev, net->e[l], net->u[l], N, H >> l, W >> l, net->ch(l + 1), net->ch(l), s));
+        NK(cv(k, net->u[l], net->da[l], l));
+        NK(cv(k + 1, net->da[l], net->d[l], l));
+        prev = net->d[l];
+        k += 2;
+    }
+    NK(conv1x1_fwd(prev, net->p + net->off_hw, net->p + net->off_hb, net->out, P0, net->ch(0), kOut, s));
+    NK(gate(net->xin, kInPad, net->out, P0, s));
     return LBPF_OK;
 }
 
 // Backward from g_out (dL/d out); accumulates parameter gradients into g.
+// Mirrors the forward pass: decoder levels from the top down (their skip
+// gradients kept), then the encoder from the deepest level up.
 int backward(lbpf_net* net)
 {
-    const int N = net->N, H = net->H, W = net->W;
-    const long long P1 = (long long)N * H * W, P2 = P1 / 4, P3 = P1 / 16;
+    const int N = net->N, H = net->H, W = net->W, lv = net->levels;
+    const long long P0 = (long long)N * H * W;
     cudaStream_t s = net->stream;
     float* g = net->g;
-    // through conv k: dY (post-ReLU grad) given, y = its output; writes dX
-    auto cvb = [&](int k, const float* in, const float* y, float* dy, float* dx, int h, int w, long long P) -> int {
+    // through conv k at level l: dY (post-ReLU grad) given, y = its output; writes dX
+    auto cvb = [&](int k, const float* in, const float* y, float* dy, float* dx, int l) -> int {
         const Conv& c = net->conv[k];
+        const int h = H >> l, w = W >> l;
+        const long long P = (long long)N * h * w;
         NK(relu_bwd(y, dy, P * c.cout, s));
         NK(conv3x3_wgrad(in, dy, g + c.off_w, N, h, w, c.cin, c.cout, s));
         NK(bias_grad(dy, g + c.off_b, P, c.cout, s));
@@ -277,27 +329,26 @@ int backward(lbpf_net* net)
         return LBPF_OK;
     };
     int rc;
-    NK(gate(net->xin, kInPad, net->g_out, P1, s));  // the gate is linear in the output
-    NK(conv1x1_bwd(net->d1, net->g_out, net->p + net->off_hw, net->g_big0, g + net->off_hw, g + net->off_hb, P1, 16,
-                   kOut, s));
-    if ((rc = cvb(9, net->d1a, net->d1, net->g_big0, net->g_big1, H, W, P1))) return rc;
-    if ((rc = cvb(8, net->u1, net->d1a, net->g_big1, net->g_cat1, H, W, P1))) return rc;
-    // u1 = [up(d2) (32), a1 (16)]
-    NK(upcat_bwd(net->g_cat1, net->g_mid0, net->g_big0, N, H, W, 32, 16, s));  // g_big0 = da1 (skip part)
-    if ((rc = cvb(7, net->d2a, net->d2, net->g_mid0, net->g_mid1, H / 2, W / 2, P2))) return rc;
-    if ((rc = cvb(6, net->u2, net->d2a, net->g_mid1, net->g_cat2, H / 2, W / 2, P2))) return rc;
-    // u2 = [up(a3) (64), a2 (32)]
-    NK(upcat_bwd(net->g_cat2, net->g_sml0, net->g_mid0, N, H / 2, W / 2, 64, 32, s));  // g_mid0 = da2 (skip part)
-    if ((rc = cvb(5, net->a3a, net->a3, net->g_sml0, net->g_sml1, H / 4, W / 4, P3))) return rc;
-    if ((rc = cvb(4, net->p2, net->a3a, net->g_sml1, net->g_sml0, H / 4, W / 4, P3))) return rc;  // g_sml0 = dp2
-    NK(pool_bwd(net->g_sml0, net->g_mid1, N, H / 2, W / 2, 32, s));
-    NK(add_inplace(net->g_mid0, net->g_mid1, P2 * 32, s));  // da2 total
-    if ((rc = cvb(3, net->a2a, net->a2, net->g_mid0, net->g_mid1, H / 2, W / 2, P2))) return rc;
-    if ((rc = cvb(2, net->p1, net->a2a, net->g_mid1, net->g_mid0, H / 2, W / 2, P2))) return rc;  // g_mid0 = dp1 (16 ch)
-    NK(pool_bwd(net->g_mid0, net->g_big1, N, H, W, 16, s));
-    NK(add_inplace(net->g_big0, net->g_big1, P1 * 16, s));  // da1 total
-    if ((rc = cvb(1, net->a1a, net->a1, net->g_big0, net->g_big1, H, W, P1))) return rc;
-    if ((rc = cvb(0, net->xin, net->a1a, net->g_big1, nullptr, H, W, P1))) return rc;
+    NK(gate(net->xin, kInPad, net->g_out, P0, s));  // the gate is linear in the output
+    NK(conv1x1_bwd(net->top(), net->g_out, net->p + net->off_hw, net->ga[0], g + net->off_hw, g + net->off_hb, P0,
+                   net->ch(0), kOut, s));
+    int k = (int)net->conv.size();
+    for (int l = 0; l + 1 < lv; ++l) {  // decoder: the gradient of d[l] is in ga[l]
+        k -= 2;
+        if ((rc = cvb(k + 1, net->da[l], net->d[l], net->ga[l], net->gb[l], l))) return rc;
+        if ((rc = cvb(k, net->u[l], net->da[l], net->gb[l], net->ga[l], l))) return rc;
+        // u[l] = [up(level l + 1 output), e[l]]
+        NK(upcat_bwd(net->ga[l], net->ga[l + 1], net->gskip[l], N, H >> l, W >> l, net->ch(l + 1), net->ch(l), s));
+    }
+    for (int l = lv - 1; l >= 0; --l) {  // encoder: the gradient of e[l] is in ga[l]
+        k -= 2;
+        const long long Pl = P0 >> (2 * l);
+        if (l + 1 < lv) NK(add_inplace(net->ga[l], net->gskip[l], Pl * net->ch(l), s));
+        if ((rc = cvb(k + 1, net->ea[l], net->e[l], net->ga[l], net->gb[l], l))) return rc;
+        if ((rc = cvb(k, l > 0 ? net->pl[l] : net->xin, net->ea[l], net->gb[l], l > 0 ? net->ga[l] : nullptr, l)))
+            return rc;
+        if (l > 0) NK(pool_bwd(net->ga[l], net->ga[l - 1], N, H >> (l - 1), W >> (l - 1), net->ch(l - 1), s));
+    }
     return LBPF_OK;
 }
 
@@ -385,7 +436,8 @@ extern "C" int lbpf_net_range_check(const float* phi, long long sites, float lo,
 extern "C" int lbpf_nn_conv3x3(const float* x, const void* wt, const float* bias, float* y, int n, int H, int W,
                                int cin, int cout, int relu, void* stream)
 {
-    if (!x || !wt || !y || n < 1 || H < 1 || W < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 || cout > 256)
+    const int n_tiles = (cout + 255) / 256;
+    if (!x || !wt || !y || n < 1 || H < 1 || W < 1 || cin < 16 || cout < 16 || cin % 16 || cout % (16 * n_tiles))
         return LBPF_EINVAL;
     return conv3x3_fwd(x, static_cast<const __nv_bfloat16*>(wt), bias, y, n, H, W, cin, cout, relu,
                        static_cast<cudaStream_t>(stream)) == cudaSuccess

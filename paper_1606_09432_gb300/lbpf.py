@@ -30,7 +30,7 @@ LBPF_BC_WALL_X, LBPF_BC_WALL_Y, LBPF_BC_WALL_Z = 1, 2, 4
 EXPORTED = ["lbpf_create", "lbpf_seed", "lbpf_write_fields", "lbpf_step", "lbpf_read_fields", "lbpf_read_field",
             "lbpf_read_populations", "lbpf_measure", "lbpf_query", "lbpf_destroy", "lbpf_last_error",
             "lbpf_field_sums_static", "lbpf_set_schedule", "lbpf_tip_velocity", "lbpf_tip_radius",
-            "lbpf_net_create", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
+            "lbpf_net_create", "lbpf_net_create_arch", "lbpf_net_destroy", "lbpf_net_last_error", "lbpf_net_num_params",
             "lbpf_net_get_params", "lbpf_net_set_params", "lbpf_net_forward", "lbpf_net_backward",
             "lbpf_net_train_step", "lbpf_net_assemble", "lbpf_net_apply", "lbpf_net_delta",
             "lbpf_net_range_check", "lbpf_net_set_loss_weight", "lbpf_nn_conv3x3", "lbpf_nn_conv3x3_wgrad",
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
     lib.lbpf_tip_velocity.argtypes = [vp, C.c_int, C.c_int, d]
     lib.lbpf_tip_radius.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, d]
     lib.lbpf_net_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp, C.POINTER(vp)]
+    lib.lbpf_net_create_arch.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp,
+                                         C.POINTER(vp)]
     lib.lbpf_net_destroy.argtypes = [vp]
     lib.lbpf_net_last_error.argtypes = [vp]
     lib.lbpf_net_num_params.argtypes = [vp, C.POINTER(C.c_longlong)]
@@ -353,13 +355,16 @@ def _dptr(t):
 
 class Net:
     """The surrogate U-Net for batches of `batch` H x W images (NHWC float32
-    CUDA tensors: input (N, H, W, 5), output (N, H, W, 2))."""
+    CUDA tensors: input (N, H, W, 5), output (N, H, W, 2)); `levels` levels
+    with base * 2^l channels at level l."""
 
-    def __init__(self, H, W, batch=1, seed=0, stream=None):
+    def __init__(self, H, W, batch=1, seed=0, stream=None, levels=3, base=16):
         self.H, self.W, self.batch = H, W, batch
+        self.levels, self.base = levels, base
         self.stream = stream
         self.h = C.c_void_p()
-        rc = load().lbpf_net_create(H, W, batch, seed, C.c_void_p(stream) if stream else None, C.byref(self.h))
+        rc = load().lbpf_net_create_arch(H, W, batch, levels, base, seed, C.c_void_p(stream) if stream else None,
+                                         C.byref(self.h))
         if rc != LBPF_OK:
             raise LbpfError(rc, load().lbpf_net_last_error(None).decode())
         n = C.c_longlong()

@@ -10,7 +10,9 @@ terms, and the exact sum where every term is an exact multiple of 2^-20
 Two kernels: 16 x 8 halo tiles where H and W allow them, pixel gathers
 otherwise.  Shapes cover a partial last tile (pixels not a multiple of 128), several
 channel blocks a tap (cin 384 in blocks of 64, 96 in blocks of 48), the
-widest accumulator (cout 256), odd image sizes and both activations."""
+widest accumulator (cout 256), two output-channel tiles (cout 384, as in
+the data gradient of the 4-level network's 384 -> 128 layer), odd image
+sizes and both activations."""
 import numpy as np
 import pytest
 
@@ -18,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 # H a multiple of 16 and W of 8: the halo-tile kernel; otherwise the gather kernel
 SHAPES = [(1, 16, 24, 16, 16), (2, 32, 16, 32, 64), (1, 16, 8, 64, 256), (1, 48, 24, 96, 32), (1, 16, 16, 384, 128),
-          (2, 12, 20, 32, 64), (1, 8, 8, 96, 32), (1, 8, 16, 64, 256), (3, 5, 7, 48, 16), (1, 1, 1, 16, 16)]
+          (1, 16, 8, 128, 384), (2, 12, 20, 32, 64), (1, 8, 8, 96, 32), (1, 8, 16, 64, 256), (1, 8, 8, 64, 384),
+          (3, 5, 7, 48, 16), (1, 1, 1, 16, 16)]
 
 
 @pytest.fixture(scope="module")

@@ -61,15 +61,27 @@ def test_bf16_rounding(U):
     assert r[4] == -2.5 and abs(r[5] - 3.140625) < 1e-12
 
 
-def test_backward_matches_finite_differences(U):
+def test_layer_list(U):
+    """The default network's layers, written out, and the 4-level 32-channel
+    one: encoder level by level, then the decoder from the deepest level up
+    with the concatenated skip (upsampled deeper channels + this level's)."""
+    assert U.layers() == [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16),
+                          (16, 16)]
+    assert U.layers((4, 32)) == [(16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (128, 256),
+                                 (256, 256), (384, 128), (128, 128), (192, 64), (64, 64), (96, 32), (32, 32)]
+    assert U.n_params((4, 32)) == sum(9 * a * b + b for a, b in U.layers((4, 32))) + 2 * 32 + 2
+
+
+@pytest.mark.parametrize("arch,size", [((3, 16), 32), ((4, 16), 32), ((2, 16), 16)])
+def test_backward_matches_finite_differences(U, arch, size):
     rng = np.random.default_rng(2)
-    p = U.init_params(3, scale_head=0.3)
+    p = U.init_params(3, scale_head=0.3, arch=arch)
     p[p.size - 2:] = 0.1
-    x = rng.standard_normal((1, 32, 32, 5))
-    t = rng.standard_normal((1, 32, 32, 2))
-    out, c = U.forward(p, x)
-    g = U.backward(p, c, 2 * (out - t))
-    loss = lambda q: ((U.forward(q, x)[0] - t) ** 2).sum()
+    x = rng.standard_normal((1, size, size, 5))
+    t = rng.standard_normal((1, size, size, 2))
+    out, c = U.forward(p, x, arch=arch)
+    g = U.backward(p, c, 2 * (out - t), arch=arch)
+    loss = lambda q: ((U.forward(q, x, arch=arch)[0] - t) ** 2).sum()
     idx = rng.choice(p.size, 24, replace=False)
     for i in idx:
         h = 1e-5 * max(1.0, abs(p[i]))
