@@ -595,9 +595,19 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         const int px = ltx + XO, py = lty + HL;  // phi frame
         const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
         // Each local population is read in the direction loop, so that only
-        // the new populations stay live.  With deviation storage the rest
-        // population comes last: its deviation d0 = -sum of the others.
+        // the new populations stay live, except for D3Q27 with full storage,
+        // which reads them all first (more loads in flight: measured 12.7
+        // against 11.1 GLUPS at 256^3 FP32; the same choice cost 5 % on
+        // D3Q19 FP32 and 12 % on D3Q19 FP16).  With deviation storage the
+        // rest population comes last: its deviation d0 = -sum of the others.
+        // Both orders round the same operations in the same sequence.
+        constexpr bool LOCAL_FIRST = QG == 27 && !DEV;
         const R phy = DEV ? s_phi[sphi(z) * RP + py * RX + px] : R(0);
+        R loc[LOCAL_FIRST ? QG : 1];
+        if constexpr (LOCAL_FIRST) {
+#pragma unroll
+            for (int i = DEV ? 1 : 0; i < QG; ++i) loc[i] = to_real(gc[(long long)(DEV ? i - 1 : i) * n + s]);
+        }
         R gnew[QG];
         R phinew = 0, d0 = 0;
 #pragma unroll
@@ -611,10 +621,10 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
             // deviation storage d_i(x) (w_i phi(x) is in cs)
             R gl, gp;
             if (!DEV) {
-                gl = to_real(gc[(long long)i * n + s]);
+                gl = LOCAL_FIRST ? loc[LOCAL_FIRST ? i : 0] : to_real(gc[(long long)i * n + s]);
                 gp = i == 0 ? gl : to_real(gc[(long long)i * n + s + off(-ex, -ey, -ez)]);
             } else if (i > 0) {
-                const R d = to_real(gc[(long long)(i - 1) * n + s]);
+                const R d = LOCAL_FIRST ? loc[LOCAL_FIRST ? i : 0] : to_real(gc[(long long)(i - 1) * n + s]);
                 d0 = sub_rn(d0, d);
                 gl = fma_rn(R(PL::w(i)), phy, d);
                 gp = to_real(gc[(long long)(i - 1) * n + s + off(-ex, -ey, -ez)]);
