@@ -359,6 +359,54 @@ def run_surrogate(args, size=1024):
     return 0
 
 
+CONV_SHAPES = [(1, 1024, 1024, 32, 32), (1, 512, 512, 64, 64), (1, 256, 256, 128, 128), (1, 128, 128, 256, 256),
+               (1, 128, 128, 384, 128), (8, 128, 128, 32, 32)]
+
+
+def run_conv(args):
+    """The surrogate's 3x3 convolution kernels alone (tensor cores): forward
+    (bias + ReLU) and weight gradient for the 4-level network's layer shapes
+    at 1024^2 and a training batch; one JSON line a shape with TFLOP/s and
+    the fraction of the measured BF16 peak (a kernel timed alone: burst)."""
+    import torch
+    from paper_1606_09432_gb300 import build as B
+    B.build()
+    from paper_1606_09432_gb300 import lbpf as L
+    L.load()
+    peak = (peaks() or {}).get("bf16_tflops")
+    torch.manual_seed(0)
+    for n, H, W, cin, cout in CONV_SHAPES:
+        x = torch.randn((n, H, W, cin), device="cuda")
+        w = (torch.randn((9, cout, cin), device="cuda") / (3 * cin ** 0.5)).to(torch.bfloat16)
+        b = torch.zeros(cout, device="cuda")
+        y = torch.empty((n, H, W, cout), device="cuda")
+        dy = torch.randn((n, H, W, cout), device="cuda")
+        dw = torch.zeros((9, cout, cin), device="cuda")
+        flops = 2.0 * n * H * W * 9 * cin * cout
+        line = {"metric": "surrogate 3x3 convolution", "shape_nhwc_cin_cout": [n, H, W, cin, cout],
+                "flop_per_call": flops, "unit": "TFLOP/s"}
+        for name, fn in (("forward", lambda: L.nn_conv3x3(x, w, b, y, relu=True)),
+                         ("weight_grad", lambda: L.nn_conv3x3_wgrad(x, dy, dw))):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps if args.steps > 0 else 10):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (args.steps if args.steps > 0 else 10)
+            tf = flops / ms / 1e9
+            line[name] = {"us": round(ms * 1e3, 1), "tflops": round(tf, 1),
+                          "frac_of_bf16_peak": round(tf / peak, 4) if peak else None}
+        line["error_word"] = L.nn_conv_error()
+        line["peak_source"] = ("MEASURED_PEAKS.json bf16_tflops (burst, of measured)" if peak else
+                               "no MEASURED_PEAKS.json")
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_replicate(args):
     """Paper-scale runs of Secs. 4.2 and 5.2 (paper_1606_09432_gb300.replicate):
     one JSON line per run, with the paper's values as context."""
@@ -412,6 +460,8 @@ def main():
     ap.add_argument("--replicate", choices=["sec42", "sec52", "all"],
                     help="paper-scale isotropy runs of Secs. 4.2 / 5.2 instead of the benchmark")
     ap.add_argument("--rep-steps", type=int, default=0, help="steps of the Sec. 4.2 run (default 1e5)")
+    ap.add_argument("--conv", action="store_true",
+                    help="time the surrogate's tensor-core 3x3 convolution kernels alone")
     ap.add_argument("--surrogate", action="store_true",
                     help="time-to-solution of surrogate + LB vs plain LB (trains a network first)")
     args = ap.parse_args()
@@ -419,6 +469,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.conv:
+        return run_conv(args)
     if args.surrogate:
         return run_surrogate(args)
     if args.replicate:
