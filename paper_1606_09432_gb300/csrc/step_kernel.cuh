@@ -594,14 +594,18 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
         };
         const int px = ltx + XO, py = lty + HL;  // phi frame
         const int cx = ltx + 1, cy = lty + HC;  // coefficient frame
-        // Each local population is read in the direction loop, so that only
-        // the new populations stay live, except for D3Q27 with full storage,
-        // which reads them all first (more loads in flight: measured 12.7
-        // against 11.1 GLUPS at 256^3 FP32; the same choice cost 5 % on
-        // D3Q19 FP32 and 12 % on D3Q19 FP16).  With deviation storage the
-        // rest population comes last: its deviation d0 = -sum of the others.
-        // Both orders round the same operations in the same sequence.
-        constexpr bool LOCAL_FIRST = QG == 27 && !DEV;
+        // Deviation storage and D2Q9 read each local population in the
+        // direction loop, so that only the new populations stay live, and
+        // round explicitly (pull_new), as the staged kernel does; with
+        // deviation storage the rest population comes last: its deviation
+        // d0 = -sum of the others.  The 3D lattices with full storage read
+        // their local populations first (more loads in flight), and D3Q15 /
+        // D3Q19 leave contraction to the compiler: measured at 256^3 FP32,
+        // D3Q15 21.3 / 20.7, D3Q19 18.9 / 16.7, D3Q27 12.7 (explicit) / 12.3
+        // GLUPS against the in-loop explicit form; reading first cost 12 %
+        // on D3Q19 FP16.
+        constexpr bool LOCAL_FIRST = !DEV && QG >= 15;
+        constexpr bool CONTRACT = !DEV && (QG == 15 || QG == 19);
         const R phy = DEV ? s_phi[sphi(z) * RP + py * RX + px] : R(0);
         R loc[LOCAL_FIRST ? QG : 1];
         if constexpr (LOCAL_FIRST) {
@@ -632,9 +636,19 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                 gl = fma_rn(R(PL::w(0)), phy, d0);
                 gp = d0;
             }
-            const R v = pull_new<R>(ex, ey, ez, R(PL::w(i)), c1, c2, cs, vx, vy, vz, gp, gl);
+            R v;
+            if constexpr (CONTRACT) {
+                R ev = R(0);
+                if (ex) ev += R(ex) * vx;
+                if (ey) ev += R(ey) * vy;
+                if (ez) ev += R(ez) * vz;
+                v = c1 * gp - c2 * gl + R(PL::w(i)) * (cs + ev);
+                phinew += v;
+            } else {
+                v = pull_new<R>(ex, ey, ez, R(PL::w(i)), c1, c2, cs, vx, vy, vz, gp, gl);
+                phinew = add_rn(phinew, v);
+            }
             gnew[i] = v;
-            phinew = add_rn(phinew, v);
         }
         if constexpr (WALLS) {
             if (bcm && on_wall(gx, gy, z)) {
