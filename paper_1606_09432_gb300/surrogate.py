@@ -11,7 +11,7 @@ Controller, per block of M jumps of K steps on one 2D domain:
      leaves phi outside [-1 - 1e-2, 1 + 1e-2] rejects the block;
   3. validation: k_v plain LB steps from the jumped state; the tip velocity of
      the jumps is compared with the LB tip velocity over those steps (LB is
-     the judge); a relative deviation above v_tol rejects the block;
+     the reference); a relative deviation above v_tol rejects the block;
   4. a rejected block is restored from the checkpoint and redone with plain LB.
 """
 from __future__ import annotations
