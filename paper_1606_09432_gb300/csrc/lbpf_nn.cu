@@ -524,7 +524,10 @@ __global__ void __launch_bounds__(kConvM) conv3x3_wgrad_tc_kernel(const float* _
 
     const int dyy = tap / 3 - 1, dxx = tap % 3 - 1;
     const long long HW = (long long)H * W;
-    const int co = co0 + tid;  // this thread's A row
+    // A rows beyond cout stay zero: clear both A buffers once
+    const int mv = cout - co0 < kConvM ? cout - co0 : kConvM;  // valid A rows
+    for (int e = tid; e < (int)(2 * a_bytes / 16); e += kConvM)
+        reinterpret_cast<uint4*>(smem_raw)[e] = make_uint4(0u, 0u, 0u, 0u);
     const uint32_t idesc = umma_idesc_bf16(kConvM, nci);
     const int S = (int)((p1 - p0 + kWgK - 1) / kWgK);
     bool ok = true;
@@ -551,30 +554,44 @@ __global__ void __launch_bounds__(kConvM) conv3x3_wgrad_tc_kernel(const float* _
             s_q[buf][tid] = q;
         }
         __syncthreads();
-        // A: row co, pixels pb .. pb + 63 of dy
-        for (int k8 = 0; k8 < kWgK / 8; ++k8) {
+        // 16-byte pieces (channel row, 8 pixels) of A = dy and B = x at the
+        // tap's neighbours.  Tiles of at least 128 channels: one row a thread,
+        // its 64 pixels unrolled (more loads in flight); narrower tiles
+        // spread the pieces over all threads, consecutive threads on
+        // consecutive channels (measured 2.4x on 32 channels, 8-27 % slower
+        // than one row a thread at 128-384)
+        auto pieceA = [&](int m, int k8) {
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const long long pp = pb + 8 * k8 + j;
-                v[j] = (co < cout && pp < p1) ? __ldg(dy + pp * cout + co) : 0.f;
+                v[j] = pp < p1 ? __ldg(dy + pp * cout + co0 + m) : 0.f;
             }
-            *reinterpret_cast<uint4*>(sA(buf) + (size_t)k8 * kConvM * 16 + tid * 16) =
+            *reinterpret_cast<uint4*>(sA(buf) + (size_t)k8 * kConvM * 16 + m * 16) =
                 make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-        }
-        // B: row ci, the same pixels' neighbours in x
-        for (int n = tid; n < nci; n += kConvM) {
-            const int ci = ci0 + n;
-            for (int k8 = 0; k8 < kWgK / 8; ++k8) {
-                float v[8];
+        };
+        auto pieceB = [&](int n, int k8) {
+            float v[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const long long q = s_q[buf][8 * k8 + j];
-                    v[j] = q >= 0 ? __ldg(x + q * cin + ci) : 0.f;
-                }
-                *reinterpret_cast<uint4*>(sB(buf) + (size_t)k8 * nci * 16 + n * 16) = make_uint4(
-                    pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+            for (int j = 0; j < 8; ++j) {
+                const long long q = s_q[buf][8 * k8 + j];
+                v[j] = q >= 0 ? __ldg(x + q * cin + ci0 + n) : 0.f;
             }
+            *reinterpret_cast<uint4*>(sB(buf) + (size_t)k8 * nci * 16 + n * 16) = make_uint4(
+                pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+        };
+        if (mv == kConvM) {
+#pragma unroll
+            for (int k8 = 0; k8 < kWgK / 8; ++k8) pieceA(tid, k8);
+        } else {
+            for (int e = tid; e < mv * (kWgK / 8); e += kConvM) pieceA(e % mv, e / mv);
+        }
+        if (nci >= kConvM) {
+            for (int n = tid; n < nci; n += kConvM)
+#pragma unroll
+                for (int k8 = 0; k8 < kWgK / 8; ++k8) pieceB(n, k8);
+        } else {
+            for (int e = tid; e < nci * (kWgK / 8); e += kConvM) pieceB(e % nci, e / nci);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -605,6 +622,7 @@ __global__ void __launch_bounds__(kConvM) conv3x3_wgrad_tc_kernel(const float* _
                            "=r"(r[7])
                          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int co = co0 + tid;  // this thread's TMEM lane = D row
             if (co < cout) {
                 float* d = dw + ((size_t)tap * cout + co) * cin + ci0 + c;
 #pragma unroll
