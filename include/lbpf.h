@@ -162,8 +162,8 @@ typedef struct {
                             f_i^(0) = w_i u (1 + e_i . v dt / (e^2 dx)),
                         whose first moment is u v dt / dx, so the recovered
                         equation is du/dt + div(u v) = kappa lap(u) + Q_u.
-                        Only with full storage (LBPF_FP64, LBPF_FP32); 0 along
-                        a 2D lattice's z and along every walled axis (the
+                        Every precision; 0 along a 2D lattice's z and along
+                        every walled axis (the
                         velocity is tangential to the walls).  Stable for
                         |v| dt / dx well below 1; the scheme adds a numerical
                         diffusion of order |v|^2 dt.  EINVAL otherwise. */

@@ -120,8 +120,8 @@ __global__ void equilibrate_kernel(const DomainDev* dp, int cur, int fcur, int a
         for (int j = 0; j < UL::Q; ++j) {
             if (!S::dev)
                 f[(long long)j * n + s] = from_real<T, R>(R(UL::w(j)) * u * (R(1) + R(adv_dot<UL>(d, j))));
-            else if (j > 0)
-                f[(long long)(j - 1) * n + s] = from_real<T, R>(R(0));
+            else if (j > 0)  // deviation from w_j u: w_j u (e_j . a)
+                f[(long long)(j - 1) * n + s] = from_real<T, R>(R(UL::w(j)) * u * R(adv_dot<UL>(d, j)));
         }
         if (S::dev) aux[s] = u - R(0.5) * ph;
     }
@@ -160,12 +160,11 @@ __global__ void heat_sync_kernel(const DomainDev* dp, int cur, int fcur, int acu
             const long long src = s + nb.off(-UL::ex(j), -UL::ey(j), -UL::ez(j));
             const R h = auxc[src] + R(0.5) * phi[src];
             R fj;
-            if (!S::dev) {
+            if (!S::dev)
                 fj = om * to_real(fc[(long long)j * n + src]) + R(UL::w(j)) * h;
-                if (d.advect && (UL::ex(j) | UL::ey(j) | UL::ez(j)))
-                    fj += R(UL::w(j)) * R(adv_dot<UL>(d, j)) * Uc[src];
-            } else
+            else
                 fj = R(UL::w(j)) * h + om * ((j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]));
+            if (d.advect && (UL::ex(j) | UL::ey(j) | UL::ez(j))) fj += R(UL::w(j)) * R(adv_dot<UL>(d, j)) * Uc[src];
             fv[j] = fj;
             u += fj;
         }
@@ -286,8 +285,8 @@ struct LauncherImpl {
     using KU = KernelLattice<UL>;
     template <int V> static constexpr int TXV = tile_x(PL::D, V);
     template <int V> static constexpr int TYV = tile_y(PL::D, V);
-    // the advective kernel (full storage; tile variant 0, with walls)
-    static constexpr bool kAdv = !S::dev;
+    // the advective kernel (tile variant 0, with walls)
+    static constexpr bool kAdv = true;
     template <int V, bool W = false, bool A = false>
     static constexpr auto kernel()
     {
@@ -305,8 +304,8 @@ struct LauncherImpl {
         kernel<V, W, A>()<<<n_blocks, TXV<V> * TYV<V>, smem_v<V, A>(), s>>>(a);
         return cudaGetLastError();
     }
-    // Tile variant 0 is built periodic, with walls and (full storage) with an
-    // advective equilibrium; the 16-row variant 1 only for periodic domains
+    // Tile variant 0 is built periodic, with walls and with an advective
+    // equilibrium; the 16-row variant 1 only for periodic domains
     // (the context selects it for nothing else).
     static cudaError_t step(int v, int kind, const StepArgs& a, int n_blocks, cudaStream_t s)
     {

@@ -356,8 +356,6 @@ extern "C" int lbpf_create(const lbpf_domain* domains, int n_domains, int lattic
         if (!std::isfinite(d.adv[0]) || !std::isfinite(d.adv[1]) || !std::isfinite(d.adv[2]))
             return fail(nullptr, LBPF_EINVAL, "domain %d: adv must be finite", k);
         if (d.adv[0] != 0.0 || d.adv[1] != 0.0 || d.adv[2] != 0.0) {
-            if (precision != LBPF_FP64 && precision != LBPF_FP32)
-                return fail(nullptr, LBPF_EINVAL, "domain %d: an advective velocity needs full storage (FP64 or FP32)", k);
             if (dim == 2 && d.adv[2] != 0.0)
                 return fail(nullptr, LBPF_EINVAL, "domain %d: adv[2] must be 0 on a 2D lattice", k);
             if (((d.bc & LBPF_BC_WALL_X) && d.adv[0] != 0.0) || ((d.bc & LBPF_BC_WALL_Y) && d.adv[1] != 0.0) ||

@@ -213,7 +213,7 @@ struct DomainDev {
     void* phi[2];       // phi field, arithmetic type
     void* aux[2];       // heat auxiliary field (see the step kernel)
     int8_t* I[2];       // crystal index field (use_index only)
-    // Advective heat equilibrium (advect only, full storage):
+    // Advective heat equilibrium (advect only):
     //   f_i^(0) = w_i u (1 + e_i . a),  a = v dt / (dx e^2)
     // (physical axes; v the domain's uniform velocity), and U = u / eta_u of
     // the aux time level, which the heat pull reads at the source node.

@@ -140,15 +140,17 @@ constexpr size_t stf_bytes(int RP)
 // reflected, and at a wall node every population whose source lies beyond
 // the wall takes the value of its mirrored partner (the bounce-back of Sec.
 // 3.3), for the phase-field and the heat populations alike.
-// ADV (full storage): domains with a uniform velocity v use the advective
-// heat equilibrium f_j^(0) = w_j u (1 + e_j . a), a = v dt / (dx e^2), so
-// the heat pull gains w_j (e_j . a) U(x - e_j), U = u^{n-1} / eta_u, read
-// from a ring of U planes staged like h; the launch stores U^n beside aux^n.
+// ADV: domains with a uniform velocity v use the advective heat equilibrium
+// f_j^(0) = w_j u (1 + e_j . a), a = v dt / (dx e^2), so the heat pull gains
+// w_j (e_j . a) U(x - e_j), U = u^{n-1} / eta_u, read from a ring of U planes
+// staged like h; the launch stores U^n beside aux^n.  With deviation storage
+// (f_j = w_j u + d_j) the same term appears: (1 - 1/eta_u) (w_j u + d_j) +
+// w_j u (1 + e_j . a) / eta_u + w_j Q_u dt = w_j h + (1 - 1/eta_u) d_j +
+// w_j (e_j . a) U.
 template <class PL, class UL, class S, int TXT, int TY, bool WALLS, bool ADV>
 __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem it, unsigned char* smem_raw)
 {
     static_assert(PL::D == 3 && UL::D == 3, "the step kernel marches along z (2D lattices through XZ)");
-    static_assert(!(ADV && S::dev), "the advective heat equilibrium is built for full storage only");
     constexpr int NT = TXT * TY;
     using R = typename S::Real;
     using T = typename S::T;
@@ -451,15 +453,15 @@ __device__ __forceinline__ void step_item(const StepArgs& args, const WorkItem i
                         const R fr = (STF && staged) ? to_real(s_f[j * RP + (py - ey) * RX + (px - ex)])
                                                      : to_real(fc[(long long)j * n + src]);
                         fj = om_u * fr + R(UL::w(j)) * hs;
-                        if constexpr (ADV) {
-                            if (advect && (ex | ey | ez)) {
-                                const R ea = R(ex) * ax + R(ey) * ay + R(ez) * az;
-                                fj += R(UL::w(j)) * ea * s_U[sh(zp - ez) * RP + (py - ey) * RX + (px - ex)];
-                            }
-                        }
                     } else {
                         const R dj = (j == 0) ? d0 : to_real(fc[(long long)(j - 1) * n + src]);
                         fj = R(UL::w(j)) * hs + om_u * dj;
+                    }
+                    if constexpr (ADV) {
+                        if (advect && (ex | ey | ez)) {
+                            const R ea = R(ex) * ax + R(ey) * ay + R(ez) * az;
+                            fj += R(UL::w(j)) * ea * s_U[sh(zp - ez) * RP + (py - ey) * RX + (px - ex)];
+                        }
                     }
                     fv[j] = fj;
                     u += fj;

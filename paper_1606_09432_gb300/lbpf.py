@@ -132,7 +132,7 @@ def make_domain(nx, ny, nz=1, *, dx, dt, W0, tau0, kappa, lam=0.0, delta=0.0, xi
                 bc=0, adv=(0.0, 0.0, 0.0)) -> lbpf_domain:
     """lam <= 0 selects lambda* (the library applies Eq. (Kinetic-Coeff) with
     beta = 0); bc: LBPF_BC_WALL_* bits (0: periodic); adv: uniform velocity
-    of the advective heat equilibrium (physical units, full storage only)."""
+    of the advective heat equilibrium (physical units)."""
     d = lbpf_domain()
     d.nx, d.ny, d.nz = nx, ny, nz
     d.bc = bc

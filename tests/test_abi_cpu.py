@@ -49,12 +49,11 @@ def test_invalid_arguments_rejected_before_gpu(L):
 
 
 def test_invalid_velocity_rejected_before_gpu(L):
-    """The advective heat equilibrium: full storage only, no z component on
-    a 2D lattice, tangential to walls, finite."""
+    """The advective heat equilibrium: no z component on a 2D lattice,
+    tangential to walls, finite."""
     def dom(nz=1, bc=0, adv=(0.1, 0.0, 0.0)):
         return L.make_domain(8, 8, nz, dx=1, dt=0.1, W0=1, tau0=1, kappa=1, bc=bc, adv=adv)
-    cases = [(dom(), L.LBPF_D2Q9_D2Q5, L.LBPF_FP32_FP16DEV),
-             (dom(), L.LBPF_D2Q9_D2Q5, L.LBPF_FP32_BF16DEV),
+    cases = [(dom(adv=(0, 0, 0.1)), L.LBPF_D2Q9_D2Q5, L.LBPF_FP32_FP16DEV),
              (dom(adv=(0, 0, 0.1)), L.LBPF_D2Q9_D2Q5, L.LBPF_FP64),
              (dom(bc=L.LBPF_BC_WALL_X), L.LBPF_D2Q9_D2Q5, L.LBPF_FP64),
              (dom(nz=8, bc=L.LBPF_BC_WALL_Z, adv=(0.1, 0.0, 0.2)), L.LBPF_D3Q15_D3Q7, L.LBPF_FP32),

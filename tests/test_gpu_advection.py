@@ -7,7 +7,8 @@ propagator, the continuum phase speed and decay).  Here the CUDA path must
 match it element by element, with the fields read between chunks of steps,
 so that the lagged heat update (heat_sync), the load launch that follows it
 and the replayed 16-step graphs all carry the advective term: FP64 within
-1e-10 on phi and u, FP32 within 1e-4.
+1e-10 on phi and u, FP32 within 1e-4, the 16-bit deviation forms within
+1e-4 (FP16) and 1e-3 (BF16, stochastic rounding).
 """
 import numpy as np
 import pytest
@@ -153,3 +154,35 @@ def test_flow_breaks_the_symmetry(L):
     # upstream (-x) against downstream (+x): the upstream tip is the longer
     # (the FP64 oracle: 29.0 against 8.4 sites, 14.4 both without flow)
     assert t1[1] - t1[0] > 5.0 and t1[1] > t0[1] > t1[0], (t0, t1)
+
+
+@pytest.mark.parametrize("precision,bar", [(2, 1e-4), (3, 1e-3), (4, 1e-3)])
+def test_dev16_advective_growth(L, O, precision, bar):
+    """16-bit deviation storage (FP16, BF16, FP16 with stochastic rounding)
+    with a flow: the stored heat deviations now carry w_j u (e_j . a), and the
+    pull adds w_j (e_j . a) U as in full storage.  Against the FP64 oracle on
+    a 40^3 periodic box through 300 steps (FP16 within 1e-4, BF16 and
+    stochastic rounding within 1e-3 on phi and u), and Sum(u - phi/2), which
+    advection conserves, to 1e-5 of its value."""
+    shape = (40, 40, 40)
+    cr = [dict(kind=3, eps=0.0, gamma=-0.02)]
+    seeds = [(20.0, 20.0, 20.0, 8.0, 0)]
+    o = oracle_run(O, 1, shape, P3, cr, seeds=seeds, adv=V3)
+    s = gpu_run(L, 1, shape, P3, cr, seeds=seeds, precision=precision, adv=V3)
+    c0 = s.measure(20, 20, 20)[2]
+    e = compare_chunks(o, s, (100, 100, 100), bar)
+    c1 = s.measure(20, 20, 20)[2]
+    print(f"precision {precision}, advective growth after 300 steps: phi {e[0]:.2e}, u {e[1]:.2e}, "
+          f"conserved drift {abs(c1 - c0) / abs(c0):.2e}")
+    assert abs(c1 - c0) <= 1e-5 * abs(c0)
+
+
+def test_fp16_advection_along_walls(L, O):
+    """FP16 deviations, walls on z, velocity in the x-y plane."""
+    shape = (15, 20, 33)
+    cr, seeds = [dict(kind=0, eps=0.04)], [(12.0, 9.0, 0.0, 6.0, 0)]
+    v = (V3[0], V3[1], 0.0)
+    o = oracle_run(O, 1, shape, P3, cr, seeds=seeds, bc=4, adv=v)
+    s = gpu_run(L, 1, shape, P3, cr, seeds=seeds, bc=4, adv=v, precision=2)
+    e = compare_chunks(o, s, (9, 60), 1e-4)
+    print(f"FP16 deviations, z walls, flow in x-y: phi {e[0]:.2e}, u {e[1]:.2e}")
