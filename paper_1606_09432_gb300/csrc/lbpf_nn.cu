@@ -21,10 +21,10 @@ namespace lbpf_nn {
 // ---- 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
 //
 // y[p][co] = act(sum_tap sum_ci x[p + tap][ci] w[tap][co][ci] + b[co]):
-// D (M = 128 pixels of the flattened (n, h, w) order) x (N = cout) with
-// K = 9 cin, one tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = 128, N = cout,
-// K = 16) per 16 input channels of one tap, the accumulator in tensor memory
-// (TMEM).  The K loop runs over stages (tap, block of KC input channels), two
+// D (M = 128 pixels of the flattened (n, h, w) order) x (N = a tile of at
+// most 256 output channels, grid y) with K = 9 cin, one
+// tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = 128, N = the tile, K = 16)
+// per 16 input channels of one tap, the accumulator in tensor memory (TMEM).  The K loop runs over stages (tap, block of KC input channels), two
 // stage buffers in shared memory: while the tensor core works on stage s - 1,
 // the 128 threads gather stage s — each thread one pixel row of A (the tap's
 // neighbour, periodic in h and w, FP32 -> BF16) and the weight pieces of B
